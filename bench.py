@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 voxel-driven backprojection (GUPS = voxel updates per second).
+
+One step = one full reconstruction of the workload: zero the L^3 volume and
+backproject every view (all steps of the hot path: the FP64 geometry fold is
+done once at set-up, projection staging and the backprojection passes run in
+the step).  Default workload: L = 512, 496 views of 1248 x 960 FP32
+projections (the RabbitCT problem size), seeded synthetic ellipsoid phantom.
+Inputs (2.4 GB of projections, a 512 MB volume) are larger than the L2, so no
+flush is needed between steps.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 oracle on
+the host cores instead (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import numpy as np  # noqa: E402
+
+METRIC = "GUPS (voxel updates/s) at 512^3 x 496, FP32 projections"
+UNIT = "GUPS"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="fp32_L512")
+    ap.add_argument("--no-variants", action="store_true", help="skip the precision variants")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--out", default=None, help="also write the JSON line to this file")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed plumbing
+
+class Dist:
+    def __init__(self, want: int):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+            self.pg = dist
+        if want != self.world and self.rank == 0:
+            print(f"note: --gpus {want} but WORLD_SIZE={self.world}", file=sys.stderr)
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        for line in Path(self.file.name).read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+
+def oracle_rate(w, host_proj, target_s: float, max_planes: int | None = None):
+    """Time the FP64 oracle on a slab of z-planes x all views; returns (GUPS, cores, sample text)."""
+    import oracle
+    threads = oracle.max_threads()
+    L = w.L
+    z0 = L // 2
+    # calibrate on one plane, then size the sample to about target_s seconds
+    t = time.perf_counter()
+    oracle.backproject(L, w.geom.det_w, w.geom.det_h, w.geom.matrices, w.origin, w.spacing, host_proj,
+                       z_range=(z0, z0 + 1), n_threads=threads)
+    one = max(time.perf_counter() - t, 1e-6)
+    planes = int(max(1, min(L, target_s / one)))
+    if max_planes:
+        planes = min(planes, max_planes)
+    za = max(0, min(L - planes, z0 - planes // 2))
+    t = time.perf_counter()
+    oracle.backproject(L, w.geom.det_w, w.geom.det_h, w.geom.matrices, w.origin, w.spacing, host_proj,
+                       z_range=(za, za + planes), n_threads=threads)
+    dt = time.perf_counter() - t
+    updates = planes * L * L * w.n_views
+    sample = (f"{planes} of {L} z-planes x {w.n_views} views ({updates:.3e} updates, {dt:.1f} s, "
+              f"FP64 oracle, OpenMP over planes)")
+    return updates / dt / 1e9, threads, sample
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def measure_variant(w, proj_dev, dtype: str, interp: str, steps: int, warmup: int, stream, check_idx=None,
+                    host=None):
+    """GUPS (and, when check_idx is given, error vs the oracle on sampled voxels) for one precision variant."""
+    import torch
+    from paper_1401_7494_gb300 import rct, tuning
+    codes = {"f32": rct.RCT_PROJ_F32, "f16": rct.RCT_PROJ_F16, "bf16": rct.RCT_PROJ_BF16}
+    tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+    interp_code = rct.RCT_INTERP_SOFT if interp == "soft" else rct.RCT_INTERP_TEX
+    data = proj_dev
+    if dtype != "f32":
+        data = torch.empty(proj_dev.shape, dtype=tdt, device=proj_dev.device)
+        rct.rct_convert_projections(proj_dev, data, proj_dev.numel(), codes[dtype], stream)
+    tun = tuning.lookup(w.L, dtype, interp)
+    out = {"tuning": tun}
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_precision(codes[dtype], interp_code)
+        bp.set_tuning(**tun)
+        for _ in range(warmup):
+            bp.reset(stream)
+            bp.backproject(data, 0, w.n_views, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            bp.reset(stream)
+            bp.backproject(data, 0, w.n_views, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out["gups"] = w.updates / (ms / 1e3) / 1e9
+        out["ms_per_step"] = ms
+        if check_idx is not None:
+            import oracle
+            vol = torch.empty((w.L,) * 3, dtype=torch.float32, device=proj_dev.device)
+            bp.read_volume(vol, stream)
+            torch.cuda.synchronize()
+            got = vol.view(-1)[torch.from_numpy(check_idx).to(vol.device)].cpu().numpy().astype(np.float64)
+            ref = oracle.backproject_voxels(w.L, w.geom.det_w, w.geom.det_h, w.geom.matrices, w.origin, w.spacing,
+                                            host, check_idx, n_threads=oracle.max_threads())
+            out["rel_rms_vs_fp64_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            out["max_abs_vs_fp64_oracle"] = float(np.abs(got - ref).max() / np.abs(ref).max())
+    del data
+    return out
+
+
+def run_ours(args, dist: Dist) -> dict | None:
+    import torch
+    import synth
+    from paper_1401_7494_gb300 import rct, tuning
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    stream = torch.cuda.current_stream()
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+
+    w = synth.workloads.named(args.workload)
+    proj = w.projections(device=dev)                    # FP32, device resident
+    torch.cuda.synchronize()
+    tun = tuning.lookup(w.L, "f32", "soft")
+    bp = rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views)
+    bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(**tun)
+
+    def step():
+        bp.reset(stream)
+        bp.backproject(proj, 0, w.n_views, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    rct.rct_profile_kernels(bp.ctx, True)
+    l0 = bp.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    kernel_ms, kernel_launches = rct.rct_profile_read(bp.ctx)
+    rct.rct_profile_kernels(bp.ctx, False)
+    launches = bp.launches - l0
+    max_ms = dist.max(ms_total)
+    total_updates = dist.sum(float(w.updates * args.steps))
+    value = total_updates / (max_ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (the backprojection pass)
+    K = tun["views_per_pass"]
+    n_launch = kernel_launches
+    avg_kernel_s = kernel_ms / max(n_launch, 1) / 1e3
+    vol_bytes = 4 * w.L ** 3
+    img_bytes = 4 * w.geom.det_w * w.geom.det_h
+    passes_per_step = -(-w.n_views // K)
+    # per step: the first pass writes only, later passes read and write; each view's image is read once
+    bytes_per_step = vol_bytes * (1 + 2 * (passes_per_step - 1)) + img_bytes * w.n_views
+    bytes_per_launch = bytes_per_step / passes_per_step
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    achieved_gbs = bytes_per_launch / avg_kernel_s / 1e9
+    upd_per_launch = w.updates / passes_per_step
+    kernel_gups = upd_per_launch / avg_kernel_s / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None,
+                "kernel": "bp_kernel (backprojection pass)", "kernel_gups": round(kernel_gups, 2),
+                "kernel_share_of_step": round(kernel_ms / ms_total, 4),
+                "algorithmic_bytes_per_launch": int(bytes_per_launch), "updates_per_launch": int(upd_per_launch),
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: L={w.L}^3 volume, {w.n_views} views of "
+                               f"{w.geom.det_w}x{w.geom.det_h} FP32 projections, seeded ellipsoid phantom",
+                   "L": w.L, "n_views": w.n_views, "det": [w.geom.det_w, w.geom.det_h], "seed": w.seed,
+                   "tuning": tun, "parallelism": f"replicas x{dist.world}",
+                   "l2": "inputs larger than L2 (2.4 GB projections, volume >= 512 MB); no flush"},
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+    }
+
+    # --- end to end through the public API with host buffers
+    if not args.no_e2e:
+        pinned = torch.empty(proj.shape, dtype=torch.float32, pin_memory=True)
+        pinned.copy_(proj)
+        vol_host = torch.empty((w.L,) * 3, dtype=torch.float32, pin_memory=True)
+        for _ in range(max(1, args.warmup // 2)):
+            bp.reset(stream)
+            bp.backproject_host(pinned, 0, w.n_views, stream)
+            bp.read_volume(vol_host, stream)
+        torch.cuda.synchronize()
+        e_steps = max(2, args.steps // 2)
+        dist.barrier()
+        t0 = time.perf_counter()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(e_steps):
+            bp.reset(stream)
+            bp.backproject_host(pinned, 0, w.n_views, stream)
+            bp.read_volume(vol_host, stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        e_ms = max(a0.elapsed_time(a1), wall * 1e3)
+        e_ms = dist.max(e_ms)
+        result["e2e"] = {"value": round(dist.sum(float(w.updates * e_steps)) / (e_ms / 1e3) / 1e9, 2), "unit": UNIT,
+                         "h2d_bytes_per_step": int(pinned.numel() * 4), "d2h_bytes_per_step": int(vol_host.numel() * 4),
+                         "steps": e_steps, "api": "rct_backproject_host + rct_read_volume (pinned host buffers)"}
+        del pinned, vol_host
+
+    bp.close()
+    host = None
+    if dist.rank == 0 and not args.no_variants:
+        host = proj.cpu().numpy()
+        L = w.L
+        rng = np.random.default_rng(7)
+        check_idx = np.unique(np.concatenate([rng.integers(0, L ** 3, size=8192),
+                                              np.arange(L * L, dtype=np.int64) + (L // 2) * L * L]))
+        import oracle
+        variants = {}
+        for dt, it in [("f32", "soft"), ("f16", "soft"), ("bf16", "soft"), ("f16", "tex"), ("f32", "tex")]:
+            ref_host = host if dt == "f32" else host   # error stated against the FP32-input FP64 oracle
+            variants[f"{dt}_{it}"] = measure_variant(w, proj, dt, it, max(2, args.steps // 2), 1, stream,
+                                                     check_idx=check_idx, host=ref_host)
+        result["variants"] = variants
+        result["variants_note"] = ("GUPS per precision variant on the same workload; error vs the FP64 oracle on "
+                                   f"FP32 projections over {check_idx.size} sampled voxels (a full z-plane + random)")
+
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        if host is None:
+            host = proj.cpu().numpy()
+        gups, cores, sample = oracle_rate(w, host, args.cpu_seconds)
+        result["cpu_baseline"] = {"value": round(gups, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                                  "sample": sample}
+    return result
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, dist: Dist) -> dict | None:
+    if dist.rank != 0:
+        return None
+    import synth
+    import oracle
+    w = synth.workloads.named(args.workload)
+    host = w.projections(device="cuda" if _cuda_ok() else "cpu").cpu().numpy()
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    rates = []
+    cores = oracle.max_threads()
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        gups, cores, sample = oracle_rate(w, host, per_step, max_planes=8)
+        if i >= args.warmup:
+            rates.append(gups)
+    value = statistics.median(rates)
+    ms_per_step = w.updates / (value * 1e9) * 1e3
+    return {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.workload}: L={w.L}^3, {w.n_views} views of {w.geom.det_w}x{w.geom.det_h}",
+                       "per_step_sample": sample},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def _cuda_ok() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def main():
+    args = parse_args()
+    dist = Dist(args.gpus)
+    try:
+        if args.impl == "reference":
+            res = run_reference(args, dist)
+        else:
+            res = run_ours(args, dist)
+    finally:
+        dist.close()
+    if dist.rank == 0 and res is not None:
+        line = json.dumps(res)
+        print(line, flush=True)
+        if args.out:
+            Path(args.out).write_text(line + "\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * rct.h -- C ABI of the GB300 voxel-driven cone-beam backprojector.
+ *
+ * The operation is the RabbitCT backprojection (the paper, Section
+ * "Algorithm", Listing 1): for each view i with projection matrix
+ * A_i in R^{3x4} and pre-filtered projection image I_i (W columns by H rows),
+ * every voxel (x, y, z) of an L^3 volume is mapped to world coordinates
+ * p = origin + (x, y, z) * spacing, projected to (u, v, w) = A_i (p, 1),
+ * de-homogenised to (u/w, v/w), and the bilinear interpolation of the four
+ * neighbouring pixels (zero outside the detector) weighted by 1/w^2 is added
+ * into the voxel.  Floor, not truncation, selects the pixel cell, so the
+ * image behaves as zero-extended (the paper's zero-padded projection buffer,
+ * Section "SIMD Vectorization").
+ *
+ * Layouts
+ *   volume      L^3 float32, z-major, x fastest: index z*L*L + y*L + x
+ *   projection  n images, each H rows of W pixels, row-major (pixel (i, j) at
+ *               j*W + i), element type as set by rct_set_precision
+ *   matrices    n_views * 12 float64, row-major 3x4 per view (A[r*4 + c]);
+ *               NOTE: the paper's listing reads its matrix column-major
+ *
+ * Conventions
+ *   - Every call returns an rct_status; on failure rct_last_error() gives a
+ *     message for the calling thread.  Argument errors are detected
+ *     synchronously.  Asynchronous CUDA faults surface as RCT_ECUDA from a
+ *     later call on the same context.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream only enqueue work on it unless
+ *     stated otherwise; results are valid once the stream reaches them.
+ *   - A context is bound to the CUDA device that is current when it is
+ *     created; later calls must be made with that device current.  A context
+ *     is not thread-safe; distinct contexts may be used from distinct threads
+ *     and streams concurrently.
+ *   - The library never falls back to a CPU computation.
+ */
+#ifndef RCT_H
+#define RCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RCT_API __attribute__((visibility("default")))
+#else
+#define RCT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rct_ctx rct_ctx;
+
+typedef enum rct_status {
+    RCT_OK = 0,
+    RCT_EINVAL = 1,    /* bad argument (null pointer, size or range) */
+    RCT_ENOMEM = 2,    /* device or host allocation failed */
+    RCT_ECUDA = 3,     /* a CUDA runtime call or kernel failed */
+    RCT_ESTATE = 4,    /* call not valid in the context's state (e.g. no geometry yet) */
+    RCT_ETIMEOUT = 5,  /* a host-side wait gave up (serving deadlines) */
+    RCT_ENOTSUP = 6    /* combination of options not supported */
+} rct_status;
+
+/* Element type of stored projections (spec precision variants). */
+typedef enum rct_proj_dtype {
+    RCT_PROJ_F32 = 0,
+    RCT_PROJ_F16 = 1,   /* IEEE binary16 */
+    RCT_PROJ_BF16 = 2   /* bfloat16 */
+} rct_proj_dtype;
+
+/* How the four taps are interpolated. */
+typedef enum rct_interp {
+    RCT_INTERP_SOFT = 0,  /* software bilinear in FP32 (the paper's Part 3); parity-gated */
+    RCT_INTERP_TEX = 1    /* texture-unit bilinear (low-precision fixed-point weights); not gated */
+} rct_interp;
+
+/* How a software-interpolated kernel fetches its four taps (Part 2). */
+typedef enum rct_gather {
+    RCT_GATHER_AUTO = 0,  /* let the library (or the tuning cache) choose */
+    RCT_GATHER_LDG = 1,   /* four predicated read-only loads from the caller's linear images */
+    RCT_GATHER_TLD4 = 2   /* one texture gather (tld4) of the 2x2 cell from a staged copy */
+} rct_gather;
+
+/* Kernel tuning.  Zero in any field means "keep the current value". */
+typedef struct rct_tuning {
+    int views_per_pass;  /* K: views accumulated in registers per volume pass, 1..32 */
+    int zrun;            /* voxels per thread along z: 1, 2, 4 or 8 */
+    int xvec;            /* voxels per thread along x: 1, 2 or 4 (4 needs L % 4 == 0) */
+    int block_x;         /* threads per block along x */
+    int block_y;         /* threads per block along y; block_x * block_y <= 512 */
+    int gather;          /* rct_gather */
+} rct_tuning;
+
+#define RCT_MAX_VIEWS_PER_PASS 32
+
+/*
+ * Create a context for an L^3 volume and a scan of n_views projections of
+ * det_w x det_h pixels, on the current CUDA device.  Allocates the device
+ * volume (L^3 floats).  The volume starts at zero.  Returns NULL on failure
+ * (see rct_last_error).  Paper: the RabbitCT module receives L, the image
+ * width and the matrices from the framework (Section "Algorithm").
+ */
+RCT_API rct_ctx *rct_create(int L, int det_w, int det_h, int n_views);
+
+/* Release every device resource of the context (synchronises its device). NULL is ignored. */
+RCT_API void rct_destroy(rct_ctx *ctx);
+
+/*
+ * Set the scan geometry: n_views row-major 3x4 FP64 matrices (pixel units:
+ * (u/w, v/w) is the column/row of the pixel hit), the world position (mm) of
+ * the centre of voxel (0,0,0) and the voxel spacing (mm) per axis.  The
+ * library folds origin and spacing into each matrix in FP64 on the host
+ * (the paper's O and MM, Section "Algorithm") and keeps its own copies; the
+ * caller's arrays may be freed on return.  RCT_EINVAL for null pointers,
+ * non-finite values or non-positive spacing.
+ */
+RCT_API rct_status rct_set_geometry(rct_ctx *ctx, const double *matrices, const double origin[3],
+                            const double spacing[3]);
+
+/*
+ * Choose the element type of the projections passed to rct_backproject and
+ * the interpolation.  Accumulation and the 1/w^2 weight stay FP32.
+ * Default: RCT_PROJ_F32, RCT_INTERP_SOFT.
+ */
+RCT_API rct_status rct_set_precision(rct_ctx *ctx, int proj_dtype, int interp);
+
+/* Override the kernel tuning (see rct_tuning).  Validated synchronously. */
+RCT_API rct_status rct_set_tuning(rct_ctx *ctx, const rct_tuning *t);
+/* Read the tuning the next launch will use (after AUTO resolution). */
+RCT_API rct_status rct_get_tuning(const rct_ctx *ctx, rct_tuning *out);
+
+/* Zero the volume.  Costs nothing on the device: the next pass overwrites instead of adding. */
+RCT_API rct_status rct_reset_volume(rct_ctx *ctx, void *stream);
+
+/*
+ * Backproject views [first_view, first_view + n) into the volume, in view
+ * order.  d_proj points to n device images (the first one belongs to view
+ * first_view) in the element type set by rct_set_precision.  The caller
+ * owns d_proj and must keep it valid and unchanged until the stream reaches
+ * the end of this call's work.  Asynchronous on `stream`; allocates nothing
+ * once the context's staging buffers exist (they are created by the first
+ * call after rct_set_precision / rct_set_tuning changes them, so make one
+ * call before capturing this into a CUDA graph).
+ * Errors: RCT_ESTATE if no geometry was set; RCT_EINVAL for a null d_proj,
+ * n < 0 or a view range outside [0, n_views).
+ */
+RCT_API rct_status rct_backproject(rct_ctx *ctx, const void *d_proj, int first_view, int n, void *stream);
+
+/*
+ * Same, with the n images in host memory (pinned memory makes the copies
+ * asynchronous and lets them overlap the kernels).  Views are copied to the
+ * device in batches through context-owned staging buffers on a second
+ * stream, overlapped with the passes of the previous batch.  Returns once
+ * all work is enqueued on `stream`; the host buffer must stay valid until the
+ * stream reaches the end of this call's work.
+ */
+RCT_API rct_status rct_backproject_host(rct_ctx *ctx, const void *h_proj, int first_view, int n, void *stream);
+
+/* Copy the volume (L^3 floats) to dst, host or device memory.  Enqueued on stream. */
+RCT_API rct_status rct_read_volume(rct_ctx *ctx, float *dst, void *stream);
+
+/* Overwrite the volume from src (host or device, L^3 floats): restores a checkpoint. */
+RCT_API rct_status rct_write_volume(rct_ctx *ctx, const float *src, void *stream);
+
+/* Device address of the volume (valid until rct_destroy); NULL on error. */
+RCT_API float *rct_volume_device_ptr(rct_ctx *ctx);
+
+/* Geometry of the context: writes L, det_w, det_h, n_views. */
+RCT_API rct_status rct_get_shape(const rct_ctx *ctx, int *L, int *det_w, int *det_h, int *n_views);
+
+/* Number of kernel launches the context has enqueued since creation. */
+RCT_API int64_t rct_launch_count(const rct_ctx *ctx);
+
+/*
+ * Measurement support.  While enabled, every backprojection kernel the
+ * context launches is bracketed by two CUDA events recorded on the launch
+ * stream.  rct_profile_read waits for the last one, returns the summed
+ * kernel time (ms) and the number of timed launches since the last read (or
+ * since enabling), and starts a new count.  Enabling creates events lazily;
+ * do not enable it inside a CUDA graph capture.
+ */
+RCT_API rct_status rct_profile_kernels(rct_ctx *ctx, int enable);
+RCT_API rct_status rct_profile_read(rct_ctx *ctx, double *kernel_ms, int64_t *kernel_launches);
+
+/*
+ * Convert n FP32 values to the storage type dtype (round to nearest, ties
+ * to even) on the device: dst receives n 16-bit values for F16/BF16 (or a
+ * copy for F32).  Projection staging for the precision variants.
+ */
+RCT_API rct_status rct_convert_projections(const float *d_src, void *d_dst, size_t n, int dtype, void *stream);
+
+/*
+ * Host-only helper (no GPU needed): the FP64 fold that rct_set_geometry
+ * applies.  For each view it writes 12 doubles, rows (u', v', w) such that
+ * for centred voxel coordinates c = (x, y, z) - (L-1)/2
+ *     u' = u - cu*w,  v' = v - cv*w,  w = w   with (u, v, w) = A (origin + (x,y,z)*spacing, 1),
+ * and the integer detector shift (cu, cv): the pixel nearest to where the
+ * volume centre projects (0 when that point is not in front of the source).
+ * fold_out: n_views * 12 doubles; shift_out: n_views * 2 ints.
+ */
+RCT_API rct_status rct_fold_geometry(int L, int n_views, const double *matrices, const double origin[3],
+                             const double spacing[3], double *fold_out, int *shift_out);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+RCT_API const char *rct_last_error(void);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+RCT_API int rct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RCT_H */

@@ -1,0 +1,658 @@
+// C ABI of the backprojector: context, FP64 geometry fold, projection staging,
+// batching of K views per volume pass, and kernel dispatch.  See include/rct.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rct.h"
+#include "rct_internal.h"
+
+using namespace rct;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rct_status fail(rct_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+rct_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(RCT_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define RCT_CUDA(call, what)                              \
+    do {                                                  \
+        cudaError_t rct_e_ = (call);                      \
+        if (rct_e_ != cudaSuccess) return cuda_fail(rct_e_, what); \
+    } while (0)
+
+size_t dtype_size(int dt) { return dt == DT_F32 ? 4 : 2; }
+
+// One staging slot: a 2D CUDA array that holds one view for texture sampling.
+struct Slot {
+    cudaArray_t arr = nullptr;
+    cudaTextureObject_t tex = 0;
+};
+
+}  // namespace
+
+struct rct_ctx {
+    int L = 0, W = 0, H = 0, n_views = 0;
+    int device = 0;
+    float *vol = nullptr;
+    bool vol_zero_pending = true;   // the volume is logically zero; the next pass overwrites
+
+    bool geometry_set = false;
+    std::vector<double> fold;       // n_views x 12, FP64: rows u', v', w over centred voxel coords
+    std::vector<int> shift;         // n_views x 2: integer detector shift (cu, cv)
+
+    int dtype = DT_F32;
+    int interp = RCT_INTERP_SOFT;
+    rct_tuning tune{};              // gather may be RCT_GATHER_AUTO here
+    bool tune_explicit_gather = false;
+
+    // texture staging: slots for two batches of K views (ring) and what they were made for
+    std::vector<Slot> slots;
+    int slot_kind = -1;             // kernel gather kind the slots serve
+    int slot_dtype = -1;
+
+    // host-input path: linear device staging (LDG) and the copy stream
+    void *lin_stage = nullptr;
+    size_t lin_stage_bytes = 0;
+    float *widen_buf = nullptr;     // BF16 -> FP32 widening for texture-filtered BF16
+    size_t widen_elems = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_filled[2] = {nullptr, nullptr};
+    cudaEvent_t ev_free[2] = {nullptr, nullptr};
+
+    int64_t launches = 0;
+
+    // optional per-launch timing (CUDA events around every backprojection kernel)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_events;  // pairs: start, stop
+    size_t prof_used = 0;
+};
+
+namespace {
+
+int effective_gather(const rct_ctx *c) {
+    if (c->interp == RCT_INTERP_TEX) return G_TEXLIN;
+    if (c->tune.gather == RCT_GATHER_LDG) return G_LDG;
+    return G_TLD4;  // AUTO and TLD4
+}
+
+rct_tuning default_tuning(int L) {
+    rct_tuning t{};
+    t.views_per_pass = 16;
+    t.zrun = 4;
+    t.xvec = 1;
+    t.block_x = 32;
+    t.block_y = 8;
+    t.gather = RCT_GATHER_AUTO;
+    (void)L;
+    return t;
+}
+
+rct_status check_ctx(const rct_ctx *c) {
+    if (!c) return fail(RCT_EINVAL, "null context");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != c->device)
+        return fail(RCT_ESTATE, "context belongs to device %d but device %d is current", c->device, dev);
+    return RCT_OK;
+}
+
+void free_slots(rct_ctx *c) {
+    for (Slot &s : c->slots) {
+        if (s.tex) cudaDestroyTextureObject(s.tex);
+        if (s.arr) cudaFreeArray(s.arr);
+    }
+    c->slots.clear();
+    c->slot_kind = -1;
+    c->slot_dtype = -1;
+}
+
+// Channel format of a staged view for the given kernel kind and projection dtype.
+cudaChannelFormatDesc slot_format(int kind, int dt) {
+    if (dt == DT_F16) return cudaCreateChannelDescHalf();
+    if (dt == DT_BF16 && kind == G_TLD4)
+        return cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned);
+    return cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat);  // F32, and BF16 widened
+}
+
+rct_status ensure_slots(rct_ctx *c, int kind, int n_slots) {
+    if (kind == G_LDG) return RCT_OK;
+    if (c->slot_kind == kind && c->slot_dtype == c->dtype && (int)c->slots.size() >= n_slots) return RCT_OK;
+    free_slots(c);
+    const cudaChannelFormatDesc fmt = slot_format(kind, c->dtype);
+    c->slots.resize(n_slots);
+    for (int i = 0; i < n_slots; ++i) {
+        Slot &s = c->slots[i];
+        const unsigned flags = (kind == G_TLD4) ? cudaArrayTextureGather : cudaArrayDefault;
+        cudaError_t e = cudaMallocArray(&s.arr, &fmt, c->W, c->H, flags);
+        if (e != cudaSuccess) {
+            free_slots(c);
+            return e == cudaErrorMemoryAllocation ? fail(RCT_ENOMEM, "staging array allocation failed")
+                                                  : cuda_fail(e, "cudaMallocArray");
+        }
+        cudaResourceDesc rd{};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = s.arr;
+        cudaTextureDesc td{};
+        td.addressMode[0] = cudaAddressModeBorder;   // zero outside the detector
+        td.addressMode[1] = cudaAddressModeBorder;
+        td.borderColor[0] = td.borderColor[1] = td.borderColor[2] = td.borderColor[3] = 0.0f;
+        td.filterMode = (kind == G_TEXLIN) ? cudaFilterModeLinear : cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        e = cudaCreateTextureObject(&s.tex, &rd, &td, nullptr);
+        if (e != cudaSuccess) {
+            free_slots(c);
+            return cuda_fail(e, "cudaCreateTextureObject");
+        }
+    }
+    c->slot_kind = kind;
+    c->slot_dtype = c->dtype;
+    return RCT_OK;
+}
+
+rct_status ensure_copy_machinery(rct_ctx *c) {
+    if (c->copy_stream) return RCT_OK;
+    RCT_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    for (int i = 0; i < 2; ++i) {
+        RCT_CUDA(cudaEventCreateWithFlags(&c->ev_filled[i], cudaEventDisableTiming), "cudaEventCreate");
+        RCT_CUDA(cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming), "cudaEventCreate");
+    }
+    return RCT_OK;
+}
+
+rct_status ensure_widen(rct_ctx *c, size_t elems) {
+    if (c->widen_elems >= elems) return RCT_OK;
+    if (c->widen_buf) cudaFree(c->widen_buf);
+    c->widen_buf = nullptr;
+    c->widen_elems = 0;
+    cudaError_t e = cudaMalloc(&c->widen_buf, elems * sizeof(float));
+    if (e != cudaSuccess) return fail(RCT_ENOMEM, "widening buffer allocation failed");
+    c->widen_elems = elems;
+    return RCT_OK;
+}
+
+LaunchConfig launch_config(const rct_ctx *c, int kind) {
+    LaunchConfig lc{};
+    lc.gather = kind;
+    lc.dtype = c->dtype;
+    lc.xv = c->tune.xvec;
+    lc.zrun = c->tune.zrun;
+    lc.bx = c->tune.block_x;
+    lc.by = c->tune.block_y;
+    return lc;
+}
+
+// FP32 view parameters for one view and kernel kind, from the FP64 fold.
+void make_view(const rct_ctx *c, int view, int kind, ViewParams *vp) {
+    const double *f = &c->fold[12 * (size_t)view];
+    double m[12];
+    std::memcpy(m, f, sizeof m);
+    int cu = c->shift[2 * view], cv = c->shift[2 * view + 1];
+    if (kind == G_TEXLIN) {
+        // Hardware filtering samples texel centres at +0.5: fold (cu + 0.5, cv + 0.5) back in.
+        for (int k = 0; k < 4; ++k) {
+            m[k] += (cu + 0.5) * m[8 + k];
+            m[4 + k] += (cv + 0.5) * m[8 + k];
+        }
+        cu = cv = 0;
+    }
+    for (int k = 0; k < 12; ++k) vp->m[k] = static_cast<float>(m[k]);
+    vp->cu = cu;
+    vp->cv = cv;
+    vp->tex = 0;
+    vp->img = nullptr;
+}
+
+cudaError_t prof_event(rct_ctx *c, cudaStream_t s) {
+    if (c->prof_used == c->prof_events.size()) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        c->prof_events.push_back(e);
+    }
+    return cudaEventRecord(c->prof_events[c->prof_used++], s);
+}
+
+cudaError_t launch(rct_ctx *c, const LaunchConfig &lc, const BpParams &p, cudaStream_t s) {
+    cudaError_t e;
+    if (c->prof_on && (e = prof_event(c, s)) != cudaSuccess) return e;
+    c->launches += 1;
+    switch (lc.gather) {
+        case G_LDG: e = launch_bp_ldg(lc, p, s); break;
+        case G_TLD4: e = launch_bp_tld4(lc, p, s); break;
+        case G_TEXLIN: e = launch_bp_texlin(lc, p, s); break;
+        default: e = cudaErrorInvalidValue;
+    }
+    if (e == cudaSuccess && c->prof_on) e = prof_event(c, s);
+    return e;
+}
+
+// Copy one view (device or host source) into a staging slot, widening BF16 for filtered textures.
+rct_status stage_view(rct_ctx *c, Slot &slot, const void *src, bool from_host, cudaStream_t s) {
+    const size_t px = (size_t)c->W * c->H;
+    const cudaMemcpyKind kind = from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (c->dtype == DT_BF16 && c->slot_kind == G_TEXLIN) {
+        const uint16_t *dev_src = static_cast<const uint16_t *>(src);
+        if (from_host) return fail(RCT_ENOTSUP, "internal: host BF16 widening needs a device copy first");
+        cudaError_t e = launch_widen_bf16(dev_src, c->widen_buf, px, s);
+        if (e != cudaSuccess) return cuda_fail(e, "widen_bf16");
+        RCT_CUDA(cudaMemcpy2DToArrayAsync(slot.arr, 0, 0, c->widen_buf, c->W * sizeof(float), c->W * sizeof(float),
+                                          c->H, cudaMemcpyDeviceToDevice, s),
+                 "cudaMemcpy2DToArrayAsync");
+        return RCT_OK;
+    }
+    const size_t row = c->W * dtype_size(c->dtype);
+    RCT_CUDA(cudaMemcpy2DToArrayAsync(slot.arr, 0, 0, src, row, row, c->H, kind, s), "cudaMemcpy2DToArrayAsync");
+    return RCT_OK;
+}
+
+rct_status validate_range(const rct_ctx *c, const void *proj, int first, int n) {
+    if (!c->geometry_set) return fail(RCT_ESTATE, "rct_set_geometry has not been called");
+    if (n < 0) return fail(RCT_EINVAL, "n = %d is negative", n);
+    if (n > 0 && !proj) return fail(RCT_EINVAL, "null projection pointer");
+    if (first < 0 || (long long)first + n > c->n_views)
+        return fail(RCT_EINVAL, "views [%d, %lld) outside [0, %d)", first, (long long)first + n, c->n_views);
+    return RCT_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int rct_version(void) { return 10000; }
+
+const char *rct_last_error(void) { return g_last_error.c_str(); }
+
+rct_status rct_fold_geometry(int L, int n_views, const double *matrices, const double origin[3],
+                             const double spacing[3], double *fold_out, int *shift_out) {
+    if (L <= 0 || n_views < 0) return fail(RCT_EINVAL, "L = %d, n_views = %d", L, n_views);
+    if ((n_views > 0 && !matrices) || !origin || !spacing || (n_views > 0 && (!fold_out || !shift_out)))
+        return fail(RCT_EINVAL, "null pointer");
+    for (int k = 0; k < 3; ++k) {
+        if (!std::isfinite(origin[k]) || !std::isfinite(spacing[k]) || !(spacing[k] > 0.0))
+            return fail(RCT_EINVAL, "origin/spacing must be finite with spacing > 0");
+    }
+    const double cen = 0.5 * (L - 1);
+    for (int v = 0; v < n_views; ++v) {
+        const double *A = matrices + 12 * (size_t)v;
+        for (int k = 0; k < 12; ++k)
+            if (!std::isfinite(A[k])) return fail(RCT_EINVAL, "matrix of view %d is not finite", v);
+        // P = A * S, S maps centred voxel coordinates to world: p_k = origin_k + (c_k + cen) * spacing_k
+        double P[12];
+        for (int r = 0; r < 3; ++r) {
+            const double *a = A + 4 * r;
+            P[4 * r + 0] = a[0] * spacing[0];
+            P[4 * r + 1] = a[1] * spacing[1];
+            P[4 * r + 2] = a[2] * spacing[2];
+            P[4 * r + 3] = a[0] * (origin[0] + cen * spacing[0]) + a[1] * (origin[1] + cen * spacing[1]) +
+                           a[2] * (origin[2] + cen * spacing[2]) + a[3];
+        }
+        // integer detector shift: the pixel nearest to where the volume centre projects
+        int cu = 0, cv = 0;
+        if (P[11] > 0.0) {
+            const double pu = P[3] / P[11], pv = P[7] / P[11];
+            if (std::fabs(pu) < 1.0e6) cu = static_cast<int>(std::lround(pu));
+            if (std::fabs(pv) < 1.0e6) cv = static_cast<int>(std::lround(pv));
+        }
+        for (int k = 0; k < 4; ++k) {
+            P[k] -= cu * P[8 + k];
+            P[4 + k] -= cv * P[8 + k];
+        }
+        std::memcpy(fold_out + 12 * (size_t)v, P, sizeof P);
+        shift_out[2 * v] = cu;
+        shift_out[2 * v + 1] = cv;
+    }
+    return RCT_OK;
+}
+
+rct_ctx *rct_create(int L, int det_w, int det_h, int n_views) {
+    if (L <= 0 || det_w <= 0 || det_h <= 0 || n_views <= 0) {
+        fail(RCT_EINVAL, "rct_create: L=%d det_w=%d det_h=%d n_views=%d must be positive", L, det_w, det_h, n_views);
+        return nullptr;
+    }
+    if (L > 2048) {
+        fail(RCT_EINVAL, "rct_create: L=%d exceeds 2048", L);
+        return nullptr;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "rct_create: cudaGetDevice");
+        return nullptr;
+    }
+    int max_w = 0, max_h = 0;
+    cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture2DGatherWidth, dev);
+    cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxTexture2DGatherHeight, dev);
+    if ((max_w > 0 && det_w > max_w) || (max_h > 0 && det_h > max_h)) {
+        fail(RCT_EINVAL, "rct_create: detector %dx%d exceeds texture limits %dx%d", det_w, det_h, max_w, max_h);
+        return nullptr;
+    }
+    rct_ctx *c = new rct_ctx();
+    c->L = L;
+    c->W = det_w;
+    c->H = det_h;
+    c->n_views = n_views;
+    c->device = dev;
+    c->tune = default_tuning(L);
+    const size_t bytes = (size_t)L * L * L * sizeof(float);
+    e = cudaMalloc(&c->vol, bytes);
+    if (e != cudaSuccess) {
+        fail(RCT_ENOMEM, "rct_create: volume allocation of %zu bytes failed (%s)", bytes, cudaGetErrorName(e));
+        delete c;
+        return nullptr;
+    }
+    c->fold.assign(12 * (size_t)n_views, 0.0);
+    c->shift.assign(2 * (size_t)n_views, 0);
+    return c;
+}
+
+void rct_destroy(rct_ctx *c) {
+    if (!c) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_slots(c);
+    if (c->vol) cudaFree(c->vol);
+    if (c->lin_stage) cudaFree(c->lin_stage);
+    if (c->widen_buf) cudaFree(c->widen_buf);
+    for (int i = 0; i < 2; ++i) {
+        if (c->ev_filled[i]) cudaEventDestroy(c->ev_filled[i]);
+        if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete c;
+}
+
+rct_status rct_set_geometry(rct_ctx *c, const double *matrices, const double origin[3], const double spacing[3]) {
+    if (!c) return fail(RCT_EINVAL, "null context");
+    if (!matrices || !origin || !spacing) return fail(RCT_EINVAL, "null geometry pointer");
+    std::vector<double> fold(12 * (size_t)c->n_views);
+    std::vector<int> shift(2 * (size_t)c->n_views);
+    rct_status st = rct_fold_geometry(c->L, c->n_views, matrices, origin, spacing, fold.data(), shift.data());
+    if (st != RCT_OK) return st;
+    c->fold.swap(fold);
+    c->shift.swap(shift);
+    c->geometry_set = true;
+    return RCT_OK;
+}
+
+rct_status rct_set_precision(rct_ctx *c, int proj_dtype, int interp) {
+    if (!c) return fail(RCT_EINVAL, "null context");
+    if (proj_dtype < RCT_PROJ_F32 || proj_dtype > RCT_PROJ_BF16) return fail(RCT_EINVAL, "unknown dtype %d", proj_dtype);
+    if (interp != RCT_INTERP_SOFT && interp != RCT_INTERP_TEX) return fail(RCT_EINVAL, "unknown interp %d", interp);
+    c->dtype = proj_dtype;
+    c->interp = interp;
+    return RCT_OK;
+}
+
+rct_status rct_set_tuning(rct_ctx *c, const rct_tuning *t) {
+    if (!c || !t) return fail(RCT_EINVAL, "null pointer");
+    rct_tuning n = c->tune;
+    if (t->views_per_pass) n.views_per_pass = t->views_per_pass;
+    if (t->zrun) n.zrun = t->zrun;
+    if (t->xvec) n.xvec = t->xvec;
+    if (t->block_x) n.block_x = t->block_x;
+    if (t->block_y) n.block_y = t->block_y;
+    if (t->gather) n.gather = t->gather;
+    if (n.views_per_pass < 1 || n.views_per_pass > KMAX)
+        return fail(RCT_EINVAL, "views_per_pass %d outside 1..%d", n.views_per_pass, KMAX);
+    if (n.zrun != 1 && n.zrun != 2 && n.zrun != 4 && n.zrun != 8) return fail(RCT_EINVAL, "zrun %d not in {1,2,4,8}", n.zrun);
+    if (n.xvec != 1 && n.xvec != 2 && n.xvec != 4) return fail(RCT_EINVAL, "xvec %d not in {1,2,4}", n.xvec);
+    if (c->L % n.xvec != 0) return fail(RCT_EINVAL, "xvec %d does not divide L = %d", n.xvec, c->L);
+    if (n.block_x < 1 || n.block_y < 1 || n.block_x * n.block_y > 512 || (n.block_x * n.block_y) % 32 != 0)
+        return fail(RCT_EINVAL, "block %dx%d: need a multiple of 32 threads, at most 512", n.block_x, n.block_y);
+    if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_TLD4) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
+    c->tune = n;
+    return RCT_OK;
+}
+
+rct_status rct_get_tuning(const rct_ctx *c, rct_tuning *out) {
+    if (!c || !out) return fail(RCT_EINVAL, "null pointer");
+    *out = c->tune;
+    const int g = effective_gather(c);
+    out->gather = (g == G_LDG) ? RCT_GATHER_LDG : RCT_GATHER_TLD4;
+    return RCT_OK;
+}
+
+rct_status rct_reset_volume(rct_ctx *c, void *stream) {
+    (void)stream;
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    c->vol_zero_pending = true;
+    return RCT_OK;
+}
+
+static rct_status materialise_zero(rct_ctx *c, cudaStream_t s) {
+    if (!c->vol_zero_pending) return RCT_OK;
+    RCT_CUDA(cudaMemsetAsync(c->vol, 0, (size_t)c->L * c->L * c->L * sizeof(float), s), "cudaMemsetAsync");
+    c->vol_zero_pending = false;
+    return RCT_OK;
+}
+
+rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n, void *stream) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if ((st = validate_range(c, d_proj, first_view, n))) return st;
+    if (n == 0) return RCT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int kind = effective_gather(c);
+    const int K = c->tune.views_per_pass;
+    if ((st = ensure_slots(c, kind, 2 * K))) return st;
+    if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
+    const LaunchConfig lc = launch_config(c, kind);
+    const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
+    const char *base = static_cast<const char *>(d_proj);
+
+    BpParams p{};
+    p.vol = c->vol;
+    p.L = c->L;
+    p.W = c->W;
+    p.H = c->H;
+    p.cen = 0.5f * (c->L - 1);
+    for (int b = 0; b < n; b += K) {
+        const int kb = std::min(K, n - b);
+        p.K = kb;
+        p.accumulate = c->vol_zero_pending ? 0 : 1;
+        for (int k = 0; k < kb; ++k) {
+            const int view = first_view + b + k;
+            ViewParams &vp = p.view[k];
+            make_view(c, view, kind, &vp);
+            const void *src = base + (size_t)(b + k) * view_bytes;
+            if (kind == G_LDG) {
+                vp.img = src;
+            } else {
+                Slot &slot = c->slots[k];
+                if ((st = stage_view(c, slot, src, false, s))) return st;
+                vp.tex = slot.tex;
+            }
+        }
+        cudaError_t e = launch(c, lc, p, s);
+        if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
+        c->vol_zero_pending = false;
+    }
+    return RCT_OK;
+}
+
+rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, int n, void *stream) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if ((st = validate_range(c, h_proj, first_view, n))) return st;
+    if (n == 0) return RCT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int kind = effective_gather(c);
+    const int K = c->tune.views_per_pass;
+    const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
+    if ((st = ensure_copy_machinery(c))) return st;
+    if ((st = ensure_slots(c, kind, 2 * K))) return st;
+    // Linear staging: all LDG input, and BF16 destined for a filtered (FP32) texture.
+    const bool linear = (kind == G_LDG) || (kind == G_TEXLIN && c->dtype == DT_BF16);
+    if (linear && c->lin_stage_bytes < 2 * K * view_bytes) {
+        if (c->lin_stage) cudaFree(c->lin_stage);
+        c->lin_stage = nullptr;
+        c->lin_stage_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->lin_stage, 2 * K * view_bytes);
+        if (e != cudaSuccess) return fail(RCT_ENOMEM, "host staging allocation failed");
+        c->lin_stage_bytes = 2 * K * view_bytes;
+    }
+    if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
+    const LaunchConfig lc = launch_config(c, kind);
+    const char *base = static_cast<const char *>(h_proj);
+
+    // Fork: the copy stream must not run ahead of work already queued on `stream`
+    // that still reads the staging buffers.
+    RCT_CUDA(cudaEventRecord(c->ev_free[0], s), "cudaEventRecord");
+    RCT_CUDA(cudaEventRecord(c->ev_free[1], s), "cudaEventRecord");
+
+    BpParams p{};
+    p.vol = c->vol;
+    p.L = c->L;
+    p.W = c->W;
+    p.H = c->H;
+    p.cen = 0.5f * (c->L - 1);
+    int batch = 0;
+    for (int b = 0; b < n; b += K, ++batch) {
+        const int g = batch & 1;
+        const int kb = std::min(K, n - b);
+        // copy stream: wait until group g's previous pass is done, then fill it
+        RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[g], 0), "cudaStreamWaitEvent");
+        for (int k = 0; k < kb; ++k) {
+            const void *src = base + (size_t)(b + k) * view_bytes;
+            if (linear) {
+                char *dst = static_cast<char *>(c->lin_stage) + (size_t)(g * K + k) * view_bytes;
+                RCT_CUDA(cudaMemcpyAsync(dst, src, view_bytes, cudaMemcpyHostToDevice, c->copy_stream), "cudaMemcpyAsync");
+            } else {
+                if ((st = stage_view(c, c->slots[g * K + k], src, true, c->copy_stream))) return st;
+            }
+        }
+        RCT_CUDA(cudaEventRecord(c->ev_filled[g], c->copy_stream), "cudaEventRecord");
+        RCT_CUDA(cudaStreamWaitEvent(s, c->ev_filled[g], 0), "cudaStreamWaitEvent");
+        p.K = kb;
+        p.accumulate = c->vol_zero_pending ? 0 : 1;
+        for (int k = 0; k < kb; ++k) {
+            const int view = first_view + b + k;
+            ViewParams &vp = p.view[k];
+            make_view(c, view, kind, &vp);
+            const char *lin = static_cast<const char *>(c->lin_stage) + (size_t)(g * K + k) * view_bytes;
+            if (kind == G_LDG) {
+                vp.img = lin;
+            } else {
+                Slot &slot = c->slots[g * K + k];
+                if (linear) {  // BF16 for a filtered texture: widen from the linear copy on `stream`
+                    if ((st = stage_view(c, slot, lin, false, s))) return st;
+                }
+                vp.tex = slot.tex;
+            }
+        }
+        cudaError_t e = launch(c, lc, p, s);
+        if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
+        c->vol_zero_pending = false;
+        RCT_CUDA(cudaEventRecord(c->ev_free[g], s), "cudaEventRecord");
+    }
+    return RCT_OK;
+}
+
+rct_status rct_read_volume(rct_ctx *c, float *dst, void *stream) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if (!dst) return fail(RCT_EINVAL, "null destination");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = materialise_zero(c, s))) return st;
+    RCT_CUDA(cudaMemcpyAsync(dst, c->vol, (size_t)c->L * c->L * c->L * sizeof(float), cudaMemcpyDefault, s),
+             "cudaMemcpyAsync(volume)");
+    return RCT_OK;
+}
+
+rct_status rct_write_volume(rct_ctx *c, const float *src, void *stream) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if (!src) return fail(RCT_EINVAL, "null source");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    RCT_CUDA(cudaMemcpyAsync(c->vol, src, (size_t)c->L * c->L * c->L * sizeof(float), cudaMemcpyDefault, s),
+             "cudaMemcpyAsync(volume)");
+    c->vol_zero_pending = false;
+    return RCT_OK;
+}
+
+float *rct_volume_device_ptr(rct_ctx *c) {
+    if (!c) {
+        fail(RCT_EINVAL, "null context");
+        return nullptr;
+    }
+    if (c->vol_zero_pending) {
+        // A caller reading the buffer directly must see zeros: materialise on the legacy stream.
+        if (materialise_zero(c, nullptr) != RCT_OK) return nullptr;
+    }
+    return c->vol;
+}
+
+rct_status rct_get_shape(const rct_ctx *c, int *L, int *det_w, int *det_h, int *n_views) {
+    if (!c) return fail(RCT_EINVAL, "null context");
+    if (L) *L = c->L;
+    if (det_w) *det_w = c->W;
+    if (det_h) *det_h = c->H;
+    if (n_views) *n_views = c->n_views;
+    return RCT_OK;
+}
+
+int64_t rct_launch_count(const rct_ctx *c) { return c ? c->launches : -1; }
+
+rct_status rct_profile_kernels(rct_ctx *c, int enable) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    c->prof_on = enable != 0;
+    c->prof_used = 0;
+    return RCT_OK;
+}
+
+rct_status rct_profile_read(rct_ctx *c, double *kernel_ms, int64_t *kernel_launches) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if (!kernel_ms || !kernel_launches) return fail(RCT_EINVAL, "null pointer");
+    double total = 0.0;
+    if (c->prof_used > 0) RCT_CUDA(cudaEventSynchronize(c->prof_events[c->prof_used - 1]), "cudaEventSynchronize");
+    for (size_t i = 0; i + 1 < c->prof_used; i += 2) {
+        float ms = 0.f;
+        RCT_CUDA(cudaEventElapsedTime(&ms, c->prof_events[i], c->prof_events[i + 1]), "cudaEventElapsedTime");
+        total += ms;
+    }
+    *kernel_ms = total;
+    *kernel_launches = static_cast<int64_t>(c->prof_used / 2);
+    c->prof_used = 0;
+    return RCT_OK;
+}
+
+rct_status rct_convert_projections(const float *d_src, void *d_dst, size_t n, int dtype, void *stream) {
+    if (n > 0 && (!d_src || !d_dst)) return fail(RCT_EINVAL, "null pointer");
+    if (dtype < RCT_PROJ_F32 || dtype > RCT_PROJ_BF16) return fail(RCT_EINVAL, "unknown dtype %d", dtype);
+    cudaError_t e = launch_convert(d_src, d_dst, n, dtype, static_cast<cudaStream_t>(stream));
+    if (e == cudaErrorMisalignedAddress) return fail(RCT_EINVAL, "source must be 16-byte and destination 8-byte aligned");
+    if (e != cudaSuccess) return cuda_fail(e, "conversion kernel");
+    return RCT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Element-type conversion of projections (staging for the reduced-precision variants).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "rct_internal.h"
+
+namespace rct {
+
+namespace {
+
+// Round-to-nearest-even narrowing of FP32 values; four per thread when aligned.
+template <int DT>
+__global__ void narrow_kernel(const float *__restrict__ src, unsigned short *__restrict__ dst, size_t n) {
+    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+    for (size_t q = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; q * 4 < n; q += stride) {
+        const size_t i = q * 4;
+        float v[4];
+        if (i + 4 <= n) {
+            const float4 t = *reinterpret_cast<const float4 *>(src + i);
+            v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else {
+            for (int k = 0; k < 4; ++k) v[k] = (i + k < n) ? src[i + k] : 0.0f;
+        }
+        unsigned short o[4];
+        for (int k = 0; k < 4; ++k) {
+            if constexpr (DT == DT_F16) o[k] = __half_as_ushort(__float2half_rn(v[k]));
+            else o[k] = __bfloat16_as_ushort(__float2bfloat16_rn(v[k]));
+        }
+        if (i + 4 <= n) {
+            uint2 packed;
+            packed.x = static_cast<unsigned>(o[0]) | (static_cast<unsigned>(o[1]) << 16);
+            packed.y = static_cast<unsigned>(o[2]) | (static_cast<unsigned>(o[3]) << 16);
+            *reinterpret_cast<uint2 *>(dst + i) = packed;
+        } else {
+            for (int k = 0; k < 4 && i + k < n; ++k) dst[i + k] = o[k];
+        }
+    }
+}
+
+__global__ void widen_bf16_kernel(const unsigned short *__restrict__ src, float *__restrict__ dst, size_t n) {
+    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+    for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] = __uint_as_float(static_cast<unsigned>(src[i]) << 16);
+}
+
+int grid_for(size_t work, int block) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t want = (work + block - 1) / block;
+    const size_t cap = static_cast<size_t>(sms) * 8;
+    return static_cast<int>(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_convert(const float *src, void *dst, size_t n, int dtype, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (dtype == DT_F32) return cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    // 16-byte vector loads need 16-byte aligned sources, 8-byte stores 8-byte aligned destinations.
+    if ((reinterpret_cast<uintptr_t>(src) & 15) || (reinterpret_cast<uintptr_t>(dst) & 7)) return cudaErrorMisalignedAddress;
+    const int block = 256;
+    const int grid = grid_for((n + 3) / 4, block);
+    auto *d = static_cast<unsigned short *>(dst);
+    if (dtype == DT_F16) narrow_kernel<DT_F16><<<grid, block, 0, s>>>(src, d, n);
+    else if (dtype == DT_BF16) narrow_kernel<DT_BF16><<<grid, block, 0, s>>>(src, d, n);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_widen_bf16(const uint16_t *src, float *dst, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int block = 256;
+    widen_bf16_kernel<<<grid_for(n, block), block, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace rct

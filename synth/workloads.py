@@ -68,9 +68,11 @@ WORKLOADS = {
     "fp32_L512": dict(L=512, seed=1402),
     "fp32_L1024": dict(L=1024, seed=1403),
     "prec_L512": dict(L=512, seed=1404),
+    # a short scan of the L=512 geometry for profiler captures (inputs still larger than L2)
+    "profile_L512": dict(L=512, seed=1402, n_views=64),
 }
 
 
 def named(name: str) -> Workload:
-    kw = WORKLOADS[name]
-    return make_workload(kw["L"], seed=kw["seed"], name=name)
+    kw = dict(WORKLOADS[name])
+    return make_workload(kw.pop("L"), name=name, **kw)

@@ -1,0 +1,63 @@
+"""Parity at the measured configurations: 496 views of 1248x960, L = 128 (every voxel) and
+L = 512 / 1024 (sampled voxels and whole planes), in the launch configuration the benchmark uses."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_1401_7494_gb300 import rct
+from paper_1401_7494_gb300 import tuning as tuning_mod
+from gpu_helpers import assert_parity, gpu_backproject, oracle_volume, DTYPES, stored, oracle_inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _sampled_reference(w, host, idx):
+    return oracle.backproject_voxels(w.L, w.geom.det_w, w.geom.det_h, w.geom.matrices, w.origin, w.spacing,
+                                     host, idx, n_threads=oracle.max_threads())
+
+
+def _sample_indices(L, seed, n_random=1 << 15, planes=(0,)):
+    rng = np.random.default_rng(seed)
+    idx = [rng.integers(0, L ** 3, size=n_random)]
+    for z in planes:
+        idx.append(np.arange(L * L, dtype=np.int64) + z * L * L)
+    # the last row of the last plane: ragged x/y tails of the grid
+    idx.append(np.arange(L, dtype=np.int64) + (L - 1) * L * L + (L - 1) * L)
+    return np.unique(np.concatenate(idx))
+
+
+def test_full_parity_L128_496_views(cuda_device):
+    w = synth.workloads.named("fp32_L128")
+    proj = w.projections(device=cuda_device)
+    host = proj.cpu().numpy()
+    got = gpu_backproject(w, proj, tuning=tuning_mod.lookup(w.L, "f32", "soft"))
+    ref = oracle_volume(w, host)
+    assert_parity(got, ref, "L=128 x 496 full volume")
+
+
+@pytest.mark.parametrize("name,dtype", [("fp32_L512", "f32"), ("fp32_L1024", "f32"), ("prec_L512", "f16"),
+                                        ("prec_L512", "bf16")])
+def test_sampled_parity_large(cuda_device, name, dtype):
+    w = synth.workloads.named(name)
+    proj = w.projections(device=cuda_device)
+    host = proj.cpu().numpy()
+    tun = tuning_mod.lookup(w.L, dtype, "soft")
+    stream = torch.cuda.current_stream()
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
+        bp.set_precision(DTYPES[dtype][0], rct.RCT_INTERP_SOFT)
+        bp.set_tuning(**tun)
+        data = stored(proj, dtype)
+        del proj
+        bp.backproject(data, 0, w.n_views, stream)
+        vol = torch.empty((w.L,) * 3, dtype=torch.float32, device=cuda_device)
+        bp.read_volume(vol, stream)
+        torch.cuda.synchronize()
+    del data
+    idx = _sample_indices(w.L, seed=w.seed, planes=(w.L // 2,))
+    got = vol.view(-1)[torch.from_numpy(idx).to(cuda_device)].cpu().numpy()
+    del vol
+    ref = _sampled_reference(w, oracle_inputs(host, dtype), idx)
+    assert_parity(got, ref, f"{name} {dtype} sampled ({idx.size} voxels)")

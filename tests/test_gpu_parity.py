@@ -1,0 +1,203 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI (needs a GPU)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_1401_7494_gb300 import rct
+from gpu_helpers import (assert_parity, gpu_backproject, oracle_inputs, oracle_volume, rel_errors,
+                         REL_RMS_TOL, MAX_ABS_TOL)
+
+pytestmark = pytest.mark.gpu
+
+# Small cases: several thread blocks and z-runs, ragged tails in x, y and z.
+SMALL = {
+    "L37": dict(L=37, n_views=20, det_w=96, det_h=74, seed=21),
+    "L40": dict(L=40, n_views=33, det_w=130, det_h=100, seed=22),
+    "L64": dict(L=64, n_views=40, det_w=160, det_h=123, seed=23),
+}
+
+
+def _case(name, device):
+    w = synth.make_workload(**SMALL[name])
+    proj = w.projections(device=device)
+    return w, proj, proj.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def small_cases(cuda_device):
+    return {k: _case(k, cuda_device) for k in SMALL}
+
+
+TUNINGS = [
+    dict(gather=rct.RCT_GATHER_TLD4),
+    dict(gather=rct.RCT_GATHER_LDG),
+    dict(gather=rct.RCT_GATHER_TLD4, views_per_pass=7, zrun=8, xvec=1, block_x=64, block_y=2),
+    dict(gather=rct.RCT_GATHER_LDG, views_per_pass=32, zrun=1, xvec=1, block_x=32, block_y=4),
+    dict(gather=rct.RCT_GATHER_TLD4, views_per_pass=3, zrun=2, xvec=2, block_x=16, block_y=16),
+]
+
+
+@pytest.mark.parametrize("case", sorted(SMALL))
+@pytest.mark.parametrize("ti", range(len(TUNINGS)))
+def test_fp32_parity_small(small_cases, case, ti):
+    w, proj, host = small_cases[case]
+    tuning = dict(TUNINGS[ti])
+    if w.L % tuning.get("xvec", 1):
+        tuning["xvec"] = 1
+    got = gpu_backproject(w, proj, tuning=tuning)
+    ref = oracle_volume(w, host)
+    assert_parity(got, ref, f"{case} tuning {tuning}")
+
+
+@pytest.mark.parametrize("case", ["L40", "L64"])
+def test_fp32_parity_xvec4(small_cases, case):
+    w, proj, host = small_cases[case]
+    got = gpu_backproject(w, proj, tuning=dict(xvec=4, block_x=8, block_y=8, zrun=4))
+    assert_parity(got, oracle_volume(w, host), f"{case} xvec=4")
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+@pytest.mark.parametrize("gather", [rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG])
+def test_reduced_precision_storage_parity(small_cases, dtype, gather):
+    """FP16/BF16 storage: same parity bar against the oracle fed the rounded projections."""
+    w, proj, host = small_cases["L40"]
+    got = gpu_backproject(w, proj, dtype=dtype, tuning=dict(gather=gather))
+    assert_parity(got, oracle_volume(w, oracle_inputs(host, dtype)), f"{dtype} storage")
+    # and the stated (not gated) error against the FP32-input oracle stays small
+    rms, _ = rel_errors(got, oracle_volume(w, host))
+    assert rms < 5e-2 if dtype == "bf16" else rms < 5e-3
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_texture_interp_error_is_bounded(small_cases, dtype):
+    """Hardware bilinear uses fixed-point weights: its error is reported, with a loose sanity bound."""
+    w, proj, host = small_cases["L64"]
+    got = gpu_backproject(w, proj, dtype=dtype, interp=rct.RCT_INTERP_TEX)
+    rms, mx = rel_errors(got, oracle_volume(w, oracle_inputs(host, dtype)))
+    assert rms < 2e-2 and mx < 5e-2, (rms, mx)
+
+
+def test_convert_projections_bit_exact(cuda_device):
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.normal(size=100003) * 10.0 ** rng.uniform(-6, 5, size=100003),
+                        [0.0, -0.0, 65504.0, 65520.0, 1e-8, 3.3895e38]]).astype(np.float32)
+    src = torch.from_numpy(x).to(cuda_device)
+    for name, code, tdt, ref in [("f16", rct.RCT_PROJ_F16, torch.float16, oracle.round_f16),
+                                 ("bf16", rct.RCT_PROJ_BF16, torch.bfloat16, oracle.round_bf16)]:
+        dst = torch.empty(x.size, dtype=tdt, device=cuda_device)
+        rct.rct_convert_projections(src, dst, x.size, code, torch.cuda.current_stream())
+        got = dst.float().cpu().numpy()
+        exp = ref(x)
+        assert np.array_equal(got, exp, equal_nan=True), name
+
+
+def test_views_per_pass_does_not_change_bits(small_cases):
+    """The per-voxel sum runs in view order whatever K is; partial sums round-trip through FP32 exactly."""
+    w, proj, _ = small_cases["L37"]
+    vols = [gpu_backproject(w, proj, tuning=dict(views_per_pass=k, zrun=4, xvec=1, gather=rct.RCT_GATHER_TLD4))
+            for k in (1, 5, 32)]
+    assert np.array_equal(vols[0], vols[1]) and np.array_equal(vols[0], vols[2])
+
+
+def test_split_calls_and_checkpoint_resume(small_cases, cuda_device):
+    w, proj, _ = small_cases["L37"]
+    tun = dict(views_per_pass=4, zrun=2, gather=rct.RCT_GATHER_LDG)
+    whole = gpu_backproject(w, proj, tuning=tun)
+    # split at a batch boundary: identical bits
+    split = gpu_backproject(w, proj, tuning=tun, chunks=[(0, 8), (8, w.n_views)])
+    assert np.array_equal(whole, split)
+    # checkpoint after 8 views, restore into a fresh context, continue
+    stream = torch.cuda.current_stream()
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as a:
+        a.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(**tun)
+        a.backproject(proj[:8], 0, 8, stream)
+        ckpt = torch.empty((w.L,) * 3, device=cuda_device)
+        a.read_volume(ckpt, stream)
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as b:
+        b.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(**tun)
+        b.write_volume(ckpt, stream)
+        b.backproject(proj[8:], 8, w.n_views - 8, stream)
+        out = torch.empty_like(ckpt)
+        b.read_volume(out, stream)
+        torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), whole)
+
+
+def test_host_input_path_matches_device_path(small_cases):
+    w, proj, host = small_cases["L40"]
+    for gather in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG):
+        tun = dict(views_per_pass=5, gather=gather)
+        dev = gpu_backproject(w, proj, tuning=tun)
+        pinned = torch.from_numpy(host).pin_memory()
+        stream = torch.cuda.current_stream()
+        with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+            bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(**tun)
+            bp.backproject_host(pinned, 0, w.n_views, stream)
+            out = np.empty((w.L,) * 3, np.float32)
+            torch.cuda.synchronize()
+            bp.read_volume(out, stream)
+            torch.cuda.synchronize()
+        assert np.array_equal(out, dev), f"gather {gather}"
+
+
+def test_reset_and_zero_volume(small_cases, cuda_device):
+    w, proj, _ = small_cases["L37"]
+    stream = torch.cuda.current_stream()
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
+        out = torch.full((w.L,) * 3, 7.0, device=cuda_device)
+        bp.read_volume(out, stream)                  # fresh context reads zeros
+        torch.cuda.synchronize()
+        assert float(out.abs().max()) == 0.0
+        bp.backproject(proj, 0, w.n_views, stream)
+        first = torch.empty_like(out)
+        bp.read_volume(first, stream)
+        bp.reset(stream)
+        bp.backproject(proj, 0, w.n_views, stream)   # after reset: same as fresh
+        second = torch.empty_like(out)
+        bp.read_volume(second, stream)
+        bp.backproject(proj[:0], 0, 0, stream)        # n == 0 is a no-op
+        torch.cuda.synchronize()
+        assert torch.equal(first, second)
+        assert bp.launches > 0
+
+
+def test_argument_errors(cuda_device):
+    w = synth.make_workload(8, n_views=4, det_w=16, det_h=12, seed=1)
+    proj = torch.zeros((4, 12, 16), device=cuda_device)
+    with rct.Backprojector(8, 16, 12, 4) as bp:
+        with pytest.raises(rct.RctError) as e:
+            bp.backproject(proj, 0, 4)
+        assert e.value.status == rct.RCT_ESTATE
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
+        for first, n in [(-1, 2), (3, 2), (0, -1)]:
+            with pytest.raises(rct.RctError) as e:
+                rct.rct_backproject(bp.ctx, proj, first, n, None)
+            assert e.value.status == rct.RCT_EINVAL
+        with pytest.raises(rct.RctError):
+            rct.rct_backproject(bp.ctx, 0, 0, 2, None)
+        for bad in [dict(views_per_pass=33), dict(zrun=3), dict(xvec=3), dict(block_x=7, block_y=1),
+                    dict(block_x=1024, block_y=1), dict(gather=9)]:
+            with pytest.raises(rct.RctError):
+                bp.set_tuning(**bad)
+        with pytest.raises(rct.RctError):
+            bp.set_precision(5, 0)
+    with pytest.raises(rct.RctError):
+        rct.rct_create(0, 16, 16, 4)
+
+
+def test_degenerate_volumes(cuda_device):
+    """L = 1 and L = 2 (smaller than every tile), and a volume entirely off the detector."""
+    for L in (1, 2, 3):
+        w = synth.make_workload(L, n_views=9, det_w=40, det_h=30, seed=30 + L)
+        proj = w.projections(device=cuda_device)
+        got = gpu_backproject(w, proj, tuning=dict(zrun=8, views_per_pass=4))
+        assert_parity(got, oracle_volume(w, proj.cpu().numpy()), f"L={L}")
+    w = synth.make_workload(12, n_views=5, det_w=40, det_h=30, seed=40)
+    w.origin = w.origin + np.array([0.0, 0.0, 5000.0])     # far above the field of view, still w > 0
+    proj = w.projections(device=cuda_device)
+    got = gpu_backproject(w, proj)
+    ref = oracle_volume(w, proj.cpu().numpy())
+    assert np.all(got == 0.0) and np.all(ref == 0.0)
