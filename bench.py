@@ -150,11 +150,12 @@ def oracle_rate(w, host_proj, target_s: float, max_planes: int | None = None):
     threads = oracle.max_threads()
     L = w.L
     z0 = L // 2
-    # calibrate on one plane, then size the sample to about target_s seconds
+    # calibrate on one plane per thread, then size the sample to about target_s seconds
+    cal = max(1, min(L, threads))
     t = time.perf_counter()
     oracle.backproject(L, w.geom.det_w, w.geom.det_h, w.geom.matrices, w.origin, w.spacing, host_proj,
-                       z_range=(z0, z0 + 1), n_threads=threads)
-    one = max(time.perf_counter() - t, 1e-6)
+                       z_range=(z0 - cal // 2, z0 - cal // 2 + cal), n_threads=threads)
+    one = max(time.perf_counter() - t, 1e-6) / cal
     planes = int(max(1, min(L, target_s / one)))
     if max_planes:
         planes = min(planes, max_planes)
@@ -249,11 +250,13 @@ def run_ours(args, dist: Dist) -> dict | None:
     rct.rct_profile_kernels(bp.ctx, True)
     l0 = bp.launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()

@@ -201,6 +201,19 @@ RCT_API rct_status rct_convert_projections(const float *d_src, void *d_dst, size
 RCT_API rct_status rct_fold_geometry(int L, int n_views, const double *matrices, const double origin[3],
                              const double spacing[3], double *fold_out, int *shift_out);
 
+/*
+ * Throughput probes (measurement support, allocate their own small buffers).
+ * rct_probe_texture: fetches per second over the whole GPU for texture fetches
+ * of one kind -- mode 0 = tld4 gather, 1 = point fetch, 2 = bilinear filtered
+ * fetch -- from a 256x256 texture of dtype RCT_PROJ_F32 or RCT_PROJ_F16 that
+ * stays cache resident; neighbouring lanes sample stride_px apart along x and
+ * each fetch advances step_px along y.  rct_probe_update_stream: bytes read +
+ * written per second by a float4 read-modify-write sweep over `bytes` of
+ * device memory (the paper's "Node Update" benchmark, Table 1).
+ */
+RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float step_px, int iters, double *rate);
+RCT_API rct_status rct_probe_update_stream(size_t bytes, double *rate);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 RCT_API const char *rct_last_error(void);
 

@@ -1,0 +1,140 @@
+"""Autotuner for the backprojection launch: views per pass K, z-run, x-vector, block shape, gather kind.
+
+Coordinate descent over the candidate lists, starting from the built-in
+default: each round varies one parameter at a time, keeping the fastest
+value, until a round changes nothing.  Each candidate is timed with CUDA
+events on a fixed run of views of the real workload (warm-up excluded), so
+the winner is picked on GUPS for that (L, dtype, interpolation).  Results go
+to the JSON cache read by ``tuning.lookup``.
+
+Usage: python -m paper_1401_7494_gb300.autotune --L 512 [--dtype f32] [--interp soft]
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import sys
+
+from . import rct, tuning
+
+CANDIDATES = {
+    "gather": [rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG],
+    "views_per_pass": [4, 8, 16, 24, 32],
+    "zrun": [1, 2, 4, 8],
+    "xvec": [1, 2, 4],
+    "block": [(32, 4), (32, 8), (32, 16), (64, 2), (64, 4), (16, 8), (16, 16), (8, 16), (128, 2)],
+}
+
+
+def _valid(L: int, t: dict) -> bool:
+    bx, by = t["block_x"], t["block_y"]
+    return L % t["xvec"] == 0 and bx * by <= 512 and (bx * by) % 32 == 0
+
+
+def time_candidate(bp, data, n_views: int, stream, reps: int = 3) -> float:
+    """Seconds per backprojection of n_views views (best of reps after one warm-up)."""
+    import torch
+    bp.reset(stream)
+    bp.backproject(data[:n_views], 0, n_views, stream)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bp.reset(stream)
+        bp.backproject(data[:n_views], 0, n_views, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return best
+
+
+def autotune(w, data, dtype: str = "f32", interp: str = "soft", n_views: int | None = None,
+             rounds: int = 3, log=print) -> tuple[dict, float, list]:
+    """Return (best tuning, its GUPS, trial log) for workload ``w`` with projections ``data`` on the device."""
+    import torch
+    stream = torch.cuda.current_stream()
+    codes = {"f32": rct.RCT_PROJ_F32, "f16": rct.RCT_PROJ_F16, "bf16": rct.RCT_PROJ_BF16}
+    n_views = n_views or min(w.n_views, 96)
+    updates = w.L ** 3 * n_views
+    cur = dict(tuning.DEFAULT)
+    if w.L % cur["xvec"]:
+        cur["xvec"] = 1
+    trials = []
+    seen = {}
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
+        bp.set_precision(codes[dtype], rct.RCT_INTERP_SOFT if interp == "soft" else rct.RCT_INTERP_TEX)
+
+        def measure(t: dict) -> float:
+            key = tuple(sorted(t.items()))
+            if key in seen:
+                return seen[key]
+            bp.set_tuning(**t)
+            s = time_candidate(bp, data, n_views, stream)
+            g = updates / s / 1e9
+            seen[key] = g
+            trials.append({"tuning": dict(t), "gups": g})
+            log(f"  {t} -> {g:.1f} GUPS")
+            return g
+
+        best = measure(cur)
+        params = ["gather", "views_per_pass", "zrun", "xvec", "block"]
+        if interp == "tex":
+            params.remove("gather")
+        for _ in range(rounds):
+            changed = False
+            for p in params:
+                for val in CANDIDATES[p]:
+                    t = dict(cur)
+                    if p == "block":
+                        t["block_x"], t["block_y"] = val
+                    else:
+                        t[p] = val
+                    if t == cur or not _valid(w.L, t):
+                        continue
+                    g = measure(t)
+                    if g > best * 1.01:
+                        best, cur, changed = g, t, True
+            if not changed:
+                break
+    return cur, best, trials
+
+
+def main(argv=None):
+    import torch
+    import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--L", type=int, nargs="+", default=[512])
+    ap.add_argument("--dtype", nargs="+", default=["f32"])
+    ap.add_argument("--interp", nargs="+", default=["soft"])
+    ap.add_argument("--views", type=int, default=96)
+    ap.add_argument("--cache", default=str(tuning.CACHE))
+    ap.add_argument("--log", default=None)
+    args = ap.parse_args(argv)
+    dev = torch.device("cuda", 0)
+    results = []
+    for L in args.L:
+        w = synth.make_workload(L, seed=1402)
+        proj = w.projections(device=dev, views=list(range(args.views)))
+        w.geom.n_views = w.geom.n_views   # geometry keeps all views; only the first args.views are used
+        for dtype, interp in itertools.product(args.dtype, args.interp):
+            data = proj
+            if dtype != "f32":
+                tdt = {"f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+                code = {"f16": rct.RCT_PROJ_F16, "bf16": rct.RCT_PROJ_BF16}[dtype]
+                data = torch.empty(proj.shape, dtype=tdt, device=dev)
+                rct.rct_convert_projections(proj, data, proj.numel(), code, torch.cuda.current_stream())
+            print(f"L={L} {dtype} {interp}:", flush=True)
+            t, g, trials = autotune(w, data, dtype, interp, n_views=args.views)
+            print(f"  best {t} -> {g:.1f} GUPS", flush=True)
+            tuning.store(L, dtype, interp, t, g, path=args.cache, extra={"trials": len(trials)})
+            results.append({"L": L, "dtype": dtype, "interp": interp, "best": t, "gups": g, "trials": trials})
+    if args.log:
+        with open(args.log, "w") as f:
+            json.dump(results, f, indent=1)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,153 @@
+// Throughput probes that give the measured peaks the backprojection is compared against
+// (the role of likwid-bench's gather microbenchmarks in the paper, Section "Gather performance").
+//
+// rct_probe_texture: every thread issues `iters` texture fetches of one kind (tld4 gather,
+// point fetch, or filtered bilinear fetch) from a small 2D texture that stays resident in the
+// texture cache, with a configurable lane-to-lane coordinate stride, and as little arithmetic
+// as the fetch results need to stay live.  Result: fetches per second over the whole GPU.
+// rct_probe_update_stream: a read-modify-write stream over a large buffer (the paper's
+// "Node Update" benchmark, Table 1): bytes read + written per second.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/rct.h"
+
+namespace {
+
+constexpr int kTexSide = 256;   // 256 x 256 texels: 256 KB FP32, within the 256 KB L1/texture cache
+
+template <int MODE>
+__global__ void __launch_bounds__(256) tex_probe_kernel(cudaTextureObject_t tex, int iters, float stride,
+                                                        float step, float *sink) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    float x = 8.0f + lane * stride + (warp & 7) * 3.0f;
+    float y = 8.0f + ((warp >> 3) & 63) * 2.0f;
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+        if constexpr (MODE == 0) {
+            const float4 g = tex2Dgather<float4>(tex, x, y, 0);
+            acc += (g.x + g.y) + (g.z + g.w);
+        } else if constexpr (MODE == 1) {
+            acc += tex2D<float>(tex, x, y);
+        } else {
+            acc += tex2D<float>(tex, x, y);
+        }
+        y += step;
+        y = (y > kTexSide - 16.0f) ? y - (kTexSide - 32.0f) : y;
+    }
+    if (acc == 1.2345e-30f) sink[0] = acc;
+}
+
+__global__ void update_stream_kernel(float4 *__restrict__ a, size_t n4, float s) {
+    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+    for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        float4 v = a[i];
+        v.x += s; v.y += s; v.z += s; v.w += s;
+        a[i] = v;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+// mode: 0 = tld4 gather (point texture), 1 = point fetch, 2 = bilinear filtered fetch.
+// dtype: RCT_PROJ_F32 or RCT_PROJ_F16 texels.  stride_px: x distance between neighbouring lanes,
+// step_px: y advance per fetch.  Writes fetches per second (whole GPU) to *rate.
+RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float step_px, int iters,
+                                     double *rate) {
+    if (!rate || mode < 0 || mode > 2 || iters <= 0 || (dtype != RCT_PROJ_F32 && dtype != RCT_PROJ_F16))
+        return RCT_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RCT_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaChannelFormatDesc fmt = (dtype == RCT_PROJ_F16) ? cudaCreateChannelDescHalf()
+                                                        : cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat);
+    cudaArray_t arr = nullptr;
+    cudaTextureObject_t tex = 0;
+    float *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rct_status st = RCT_ECUDA;
+    do {
+        if (cudaMallocArray(&arr, &fmt, kTexSide, kTexSide, mode == 0 ? cudaArrayTextureGather : 0) != cudaSuccess) break;
+        if (cudaMalloc(&sink, sizeof(float)) != cudaSuccess) break;
+        cudaResourceDesc rd{};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = arr;
+        cudaTextureDesc td{};
+        td.addressMode[0] = td.addressMode[1] = cudaAddressModeBorder;
+        td.filterMode = (mode == 2) ? cudaFilterModeLinear : cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        if (cudaCreateTextureObject(&tex, &rd, &td, nullptr) != cudaSuccess) break;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) break;
+        const int block = 256, grid = sms * 8;
+        auto run = [&]() {
+            if (mode == 0) tex_probe_kernel<0><<<grid, block>>>(tex, iters, stride_px, step_px, sink);
+            else if (mode == 1) tex_probe_kernel<1><<<grid, block>>>(tex, iters, stride_px, step_px, sink);
+            else tex_probe_kernel<2><<<grid, block>>>(tex, iters, stride_px, step_px, sink);
+        };
+        run();
+        if (cudaDeviceSynchronize() != cudaSuccess) break;
+        float best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(e0);
+            run();
+            cudaEventRecord(e1);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = ms < best ? ms : best;
+        }
+        *rate = static_cast<double>(grid) * block * iters / (best * 1e-3);
+        st = RCT_OK;
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (tex) cudaDestroyTextureObject(tex);
+    if (arr) cudaFreeArray(arr);
+    if (sink) cudaFree(sink);
+    return st;
+}
+
+// Read-modify-write stream over `bytes` of device memory (allocated here); writes bytes moved per second.
+RCT_API rct_status rct_probe_update_stream(size_t bytes, double *rate) {
+    if (!rate || bytes < (1u << 20)) return RCT_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RCT_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    float4 *a = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rct_status st = RCT_ECUDA;
+    const size_t n4 = bytes / sizeof(float4);
+    do {
+        if (cudaMalloc(&a, n4 * sizeof(float4)) != cudaSuccess) { st = RCT_ENOMEM; break; }
+        if (cudaMemset(a, 0, n4 * sizeof(float4)) != cudaSuccess) break;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) break;
+        const int block = 512, grid = sms * 4;
+        update_stream_kernel<<<grid, block>>>(a, n4, 1.0f);
+        if (cudaDeviceSynchronize() != cudaSuccess) break;
+        float best = 1e30f;
+        for (int r = 0; r < 5; ++r) {
+            cudaEventRecord(e0);
+            update_stream_kernel<<<grid, block>>>(a, n4, 1.0f);
+            cudaEventRecord(e1);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = ms < best ? ms : best;
+        }
+        *rate = 2.0 * static_cast<double>(n4 * sizeof(float4)) / (best * 1e-3);
+        st = RCT_OK;
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (a) cudaFree(a);
+    return st;
+}
+
+}  // extern "C"

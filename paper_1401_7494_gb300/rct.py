@@ -65,6 +65,8 @@ SIGNATURES = {
     "rct_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "rct_convert_projections": (_I, [_P, _P, ctypes.c_size_t, _I, _P]),
     "rct_fold_geometry": (_I, [_I, _I, _D3, _D3, _D3, _D3, ctypes.POINTER(_I)]),
+    "rct_probe_texture": (_I, [_I, _I, ctypes.c_float, ctypes.c_float, _I, ctypes.POINTER(ctypes.c_double)]),
+    "rct_probe_update_stream": (_I, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]),
     "rct_last_error": (ctypes.c_char_p, []),
     "rct_version": (_I, []),
 }
@@ -222,6 +224,18 @@ def rct_profile_read(ctx) -> tuple[float, int]:
 
 def rct_convert_projections(d_src, d_dst, n: int, dtype: int, stream=None) -> None:
     _check(lib().rct_convert_projections(_addr(d_src), _addr(d_dst), n, dtype, _stream(stream)))
+
+
+def rct_probe_texture(mode: int, dtype: int, stride_px: float, step_px: float, iters: int = 4096) -> float:
+    r = ctypes.c_double()
+    _check(lib().rct_probe_texture(mode, dtype, stride_px, step_px, iters, ctypes.byref(r)))
+    return r.value
+
+
+def rct_probe_update_stream(nbytes: int) -> float:
+    r = ctypes.c_double()
+    _check(lib().rct_probe_update_stream(nbytes, ctypes.byref(r)))
+    return r.value
 
 
 def rct_fold_geometry(L: int, matrices, origin, spacing):
