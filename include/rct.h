@@ -172,6 +172,34 @@ RCT_API rct_status rct_get_shape(const rct_ctx *ctx, int *L, int *det_w, int *de
 RCT_API int64_t rct_launch_count(const rct_ctx *ctx);
 
 /*
+ * Allocate, now, the staging resources that rct_backproject (and, when
+ * host_input != 0, rct_backproject_host) will use with the current precision
+ * and tuning, so that later calls allocate nothing and can be captured into
+ * a CUDA graph.
+ */
+RCT_API rct_status rct_prepare(rct_ctx *ctx, int host_input);
+
+/* Device bytes a context of this shape holds once prepared (volume + staging); 0 for bad input. */
+RCT_API size_t rct_footprint_bytes(int L, int det_w, int det_h, int proj_dtype, int views_per_pass, int host_input);
+
+/*
+ * CUDA-graph capture of a sequence of calls on one stream (thread-local
+ * capture mode).  Between rct_graph_begin(stream) and rct_graph_end(stream,
+ * &g) every rct_* call on `stream` is recorded instead of run; the contexts
+ * involved must have been prepared (rct_prepare) so that nothing allocates.
+ * Kernel parameters (matrices, view range, pointers, the overwrite flag of a
+ * first pass after a reset) are frozen into the graph; the caller keeps the
+ * buffers it names alive while the graph exists.  rct_graph_launch replays
+ * it on any stream; rct_graph_destroy releases it.  The default stream
+ * cannot be captured (RCT_EINVAL).
+ */
+typedef struct rct_graph rct_graph;
+RCT_API rct_status rct_graph_begin(void *stream);
+RCT_API rct_status rct_graph_end(void *stream, rct_graph **out);
+RCT_API rct_status rct_graph_launch(rct_graph *graph, void *stream);
+RCT_API void rct_graph_destroy(rct_graph *graph);
+
+/*
  * Measurement support.  While enabled, every backprojection kernel the
  * context launches is bracketed by two CUDA events recorded on the launch
  * stream.  rct_profile_read waits for the last one, returns the summed

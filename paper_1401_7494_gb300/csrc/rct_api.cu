@@ -266,6 +266,28 @@ rct_status stage_view(rct_ctx *c, Slot &slot, const void *src, bool from_host, c
     return RCT_OK;
 }
 
+// Everything the host-input path needs: copy stream and events, 2K texture slots (two
+// batches in flight), linear staging for LDG input and for BF16 bound to a filtered texture.
+rct_status ensure_host_staging(rct_ctx *c) {
+    rct_status st;
+    const int kind = effective_gather(c);
+    const int K = c->tune.views_per_pass;
+    const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
+    if ((st = ensure_copy_machinery(c))) return st;
+    if ((st = ensure_slots(c, kind, 2 * K))) return st;
+    const bool linear = (kind == G_LDG) || (kind == G_TEXLIN && c->dtype == DT_BF16);
+    if (linear && c->lin_stage_bytes < 2 * K * view_bytes) {
+        if (c->lin_stage) cudaFree(c->lin_stage);
+        c->lin_stage = nullptr;
+        c->lin_stage_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->lin_stage, 2 * K * view_bytes);
+        if (e != cudaSuccess) return fail(RCT_ENOMEM, "host staging allocation failed");
+        c->lin_stage_bytes = 2 * K * view_bytes;
+    }
+    if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
+    return RCT_OK;
+}
+
 rct_status validate_range(const rct_ctx *c, const void *proj, int first, int n) {
     if (!c->geometry_set) return fail(RCT_ESTATE, "rct_set_geometry has not been called");
     if (n < 0) return fail(RCT_EINVAL, "n = %d is negative", n);
@@ -462,7 +484,7 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int kind = effective_gather(c);
     const int K = c->tune.views_per_pass;
-    if ((st = ensure_slots(c, kind, 2 * K))) return st;
+    if ((st = ensure_slots(c, kind, K))) return st;
     if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
     const LaunchConfig lc = launch_config(c, kind);
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
@@ -507,19 +529,8 @@ rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, 
     const int kind = effective_gather(c);
     const int K = c->tune.views_per_pass;
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
-    if ((st = ensure_copy_machinery(c))) return st;
-    if ((st = ensure_slots(c, kind, 2 * K))) return st;
-    // Linear staging: all LDG input, and BF16 destined for a filtered (FP32) texture.
+    if ((st = ensure_host_staging(c))) return st;
     const bool linear = (kind == G_LDG) || (kind == G_TEXLIN && c->dtype == DT_BF16);
-    if (linear && c->lin_stage_bytes < 2 * K * view_bytes) {
-        if (c->lin_stage) cudaFree(c->lin_stage);
-        c->lin_stage = nullptr;
-        c->lin_stage_bytes = 0;
-        cudaError_t e = cudaMalloc(&c->lin_stage, 2 * K * view_bytes);
-        if (e != cudaSuccess) return fail(RCT_ENOMEM, "host staging allocation failed");
-        c->lin_stage_bytes = 2 * K * view_bytes;
-    }
-    if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
     const LaunchConfig lc = launch_config(c, kind);
     const char *base = static_cast<const char *>(h_proj);
 
@@ -620,6 +631,70 @@ rct_status rct_get_shape(const rct_ctx *c, int *L, int *det_w, int *det_h, int *
 }
 
 int64_t rct_launch_count(const rct_ctx *c) { return c ? c->launches : -1; }
+
+rct_status rct_prepare(rct_ctx *c, int host_input) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    const int kind = effective_gather(c);
+    if ((st = ensure_slots(c, kind, c->tune.views_per_pass))) return st;
+    if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
+    if (host_input && (st = ensure_host_staging(c))) return st;
+    return RCT_OK;
+}
+
+size_t rct_footprint_bytes(int L, int det_w, int det_h, int proj_dtype, int views_per_pass, int host_input) {
+    if (L <= 0 || det_w <= 0 || det_h <= 0 || views_per_pass <= 0) return 0;
+    const size_t vol = (size_t)L * L * L * sizeof(float);
+    const size_t px = (size_t)det_w * det_h;
+    const size_t esz = dtype_size(proj_dtype);
+    const size_t slots = (size_t)(host_input ? 2 : 1) * views_per_pass;
+    size_t bytes = vol + slots * px * (proj_dtype == DT_BF16 ? 4 : esz);   // BF16 may be widened for TEX
+    if (host_input) bytes += 2 * (size_t)views_per_pass * px * esz;         // linear staging (worst case)
+    return bytes;
+}
+
+struct rct_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+rct_status rct_graph_begin(void *stream) {
+    if (!stream) return fail(RCT_EINVAL, "graph capture needs a non-default stream");
+    RCT_CUDA(cudaStreamBeginCapture(static_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal),
+             "cudaStreamBeginCapture");
+    return RCT_OK;
+}
+
+rct_status rct_graph_end(void *stream, rct_graph **out) {
+    if (!stream || !out) return fail(RCT_EINVAL, "null argument");
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    RCT_CUDA(cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &g), "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    rct_graph *r = new rct_graph();
+    r->graph = g;
+    r->exec = exec;
+    *out = r;
+    return RCT_OK;
+}
+
+rct_status rct_graph_launch(rct_graph *g, void *stream) {
+    if (!g) return fail(RCT_EINVAL, "null graph");
+    RCT_CUDA(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), "cudaGraphLaunch");
+    return RCT_OK;
+}
+
+void rct_graph_destroy(rct_graph *g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
 
 rct_status rct_profile_kernels(rct_ctx *c, int enable) {
     rct_status st = check_ctx(c);

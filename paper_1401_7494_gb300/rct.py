@@ -65,6 +65,12 @@ SIGNATURES = {
     "rct_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "rct_convert_projections": (_I, [_P, _P, ctypes.c_size_t, _I, _P]),
     "rct_fold_geometry": (_I, [_I, _I, _D3, _D3, _D3, _D3, ctypes.POINTER(_I)]),
+    "rct_prepare": (_I, [_P, _I]),
+    "rct_footprint_bytes": (ctypes.c_size_t, [_I, _I, _I, _I, _I, _I]),
+    "rct_graph_begin": (_I, [_P]),
+    "rct_graph_end": (_I, [_P, ctypes.POINTER(_P)]),
+    "rct_graph_launch": (_I, [_P, _P]),
+    "rct_graph_destroy": (None, [_P]),
     "rct_probe_texture": (_I, [_I, _I, ctypes.c_float, ctypes.c_float, _I, ctypes.POINTER(ctypes.c_double)]),
     "rct_probe_update_stream": (_I, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]),
     "rct_last_error": (ctypes.c_char_p, []),
@@ -224,6 +230,34 @@ def rct_profile_read(ctx) -> tuple[float, int]:
 
 def rct_convert_projections(d_src, d_dst, n: int, dtype: int, stream=None) -> None:
     _check(lib().rct_convert_projections(_addr(d_src), _addr(d_dst), n, dtype, _stream(stream)))
+
+
+def rct_prepare(ctx, host_input: bool = False) -> None:
+    _check(lib().rct_prepare(ctx, 1 if host_input else 0))
+
+
+def rct_footprint_bytes(L: int, det_w: int, det_h: int, proj_dtype: int, views_per_pass: int,
+                        host_input: bool = False) -> int:
+    return int(lib().rct_footprint_bytes(L, det_w, det_h, proj_dtype, views_per_pass, 1 if host_input else 0))
+
+
+def rct_graph_begin(stream) -> None:
+    _check(lib().rct_graph_begin(_stream(stream)))
+
+
+def rct_graph_end(stream) -> int:
+    g = ctypes.c_void_p()
+    _check(lib().rct_graph_end(_stream(stream), ctypes.byref(g)))
+    return g.value
+
+
+def rct_graph_launch(graph, stream=None) -> None:
+    _check(lib().rct_graph_launch(graph, _stream(stream)))
+
+
+def rct_graph_destroy(graph) -> None:
+    if graph:
+        lib().rct_graph_destroy(graph)
 
 
 def rct_probe_texture(mode: int, dtype: int, stride_px: float, step_px: float, iters: int = 4096) -> float:
