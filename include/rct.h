@@ -78,7 +78,9 @@ typedef enum rct_interp {
 typedef enum rct_gather {
     RCT_GATHER_AUTO = 0,  /* let the library (or the tuning cache) choose */
     RCT_GATHER_LDG = 1,   /* four predicated read-only loads from the caller's linear images */
-    RCT_GATHER_TLD4 = 2   /* one texture gather (tld4) of the 2x2 cell from a staged copy */
+    RCT_GATHER_TLD4 = 2,  /* one texture gather (tld4) of the 2x2 cell from a staged copy */
+    RCT_GATHER_MIX = 3    /* per z-run: the first tex_zrun positions by tld4, the rest by loads, so the
+                             texture and load/store pipes work side by side */
 } rct_gather;
 
 /* Kernel tuning.  Zero in any field means "keep the current value". */
@@ -89,6 +91,7 @@ typedef struct rct_tuning {
     int block_x;         /* threads per block along x */
     int block_y;         /* threads per block along y; block_x * block_y <= 512 */
     int gather;          /* rct_gather */
+    int tex_zrun;        /* RCT_GATHER_MIX: z positions per run fetched by tld4, 1..zrun-1 */
 } rct_tuning;
 
 #define RCT_MAX_VIEWS_PER_PASS 32

@@ -19,7 +19,10 @@ import sys
 from . import rct, tuning
 
 CANDIDATES = {
-    "gather": [rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG],
+    # (gather route, z positions per run through the texture gather when mixed)
+    "gather": [(rct.RCT_GATHER_TLD4, 0), (rct.RCT_GATHER_LDG, 0), (rct.RCT_GATHER_MIX, 1),
+               (rct.RCT_GATHER_MIX, 2), (rct.RCT_GATHER_MIX, 3), (rct.RCT_GATHER_MIX, 4),
+               (rct.RCT_GATHER_MIX, 5), (rct.RCT_GATHER_MIX, 6)],
     "views_per_pass": [4, 8, 16, 24, 32],
     "zrun": [1, 2, 4, 8],
     "xvec": [1, 2, 4],
@@ -29,6 +32,8 @@ CANDIDATES = {
 
 def _valid(L: int, t: dict) -> bool:
     bx, by = t["block_x"], t["block_y"]
+    if t.get("gather") == rct.RCT_GATHER_MIX and not (1 <= t.get("tex_zrun", 0) < t["zrun"]):
+        return False
     return L % t["xvec"] == 0 and bx * by <= 512 and (bx * by) % 32 == 0
 
 
@@ -90,6 +95,8 @@ def autotune(w, data, dtype: str = "f32", interp: str = "soft", n_views: int | N
                     t = dict(cur)
                     if p == "block":
                         t["block_x"], t["block_y"] = val
+                    elif p == "gather":
+                        t["gather"], t["tex_zrun"] = val
                     else:
                         t[p] = val
                     if t == cur or not _valid(w.L, t):
@@ -118,7 +125,6 @@ def main(argv=None):
     for L in args.L:
         w = synth.make_workload(L, seed=1402)
         proj = w.projections(device=dev, views=list(range(args.views)))
-        w.geom.n_views = w.geom.n_views   # geometry keeps all views; only the first args.views are used
         for dtype, interp in itertools.product(args.dtype, args.interp):
             data = proj
             if dtype != "f32":

@@ -88,10 +88,25 @@ struct rct_ctx {
 
 namespace {
 
-int effective_gather(const rct_ctx *c) {
-    if (c->interp == RCT_INTERP_TEX) return G_TEXLIN;
-    if (c->tune.gather == RCT_GATHER_LDG) return G_LDG;
-    return G_TLD4;  // AUTO and TLD4
+int kernel_kind(const rct_ctx *c) { return c->interp == RCT_INTERP_TEX ? G_TEXLIN : G_SOFT; }
+
+// Number of z positions of each run that fetch through the texture gather (the rest load
+// from the linear image).  LDG: none; TLD4 (and AUTO): all; MIX: the tuned split.
+int tex_zrun_of(const rct_ctx *c) {
+    const int R = c->tune.zrun;
+    switch (c->tune.gather) {
+        case RCT_GATHER_LDG: return 0;
+        case RCT_GATHER_MIX: return R <= 1 ? R : std::min(std::max(c->tune.tex_zrun, 1), R - 1);
+        default: return R;
+    }
+}
+
+bool uses_tex(const rct_ctx *c) { return kernel_kind(c) == G_TEXLIN || tex_zrun_of(c) > 0; }
+
+// The kernel reads the linear image (LDG route), or BF16 must be widened before a filtered texture.
+bool uses_linear(const rct_ctx *c) {
+    if (kernel_kind(c) == G_TEXLIN) return c->dtype == DT_BF16;
+    return tex_zrun_of(c) < c->tune.zrun;
 }
 
 rct_tuning default_tuning(int L) {
@@ -129,20 +144,21 @@ void free_slots(rct_ctx *c) {
 // Channel format of a staged view for the given kernel kind and projection dtype.
 cudaChannelFormatDesc slot_format(int kind, int dt) {
     if (dt == DT_F16) return cudaCreateChannelDescHalf();
-    if (dt == DT_BF16 && kind == G_TLD4)
+    if (dt == DT_BF16 && kind == G_SOFT)
         return cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned);
     return cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat);  // F32, and BF16 widened
 }
 
-rct_status ensure_slots(rct_ctx *c, int kind, int n_slots) {
-    if (kind == G_LDG) return RCT_OK;
+rct_status ensure_slots(rct_ctx *c, int n_slots) {
+    if (!uses_tex(c)) return RCT_OK;
+    const int kind = kernel_kind(c);
     if (c->slot_kind == kind && c->slot_dtype == c->dtype && (int)c->slots.size() >= n_slots) return RCT_OK;
     free_slots(c);
     const cudaChannelFormatDesc fmt = slot_format(kind, c->dtype);
     c->slots.resize(n_slots);
     for (int i = 0; i < n_slots; ++i) {
         Slot &s = c->slots[i];
-        const unsigned flags = (kind == G_TLD4) ? cudaArrayTextureGather : cudaArrayDefault;
+        const unsigned flags = (kind == G_SOFT) ? cudaArrayTextureGather : cudaArrayDefault;
         cudaError_t e = cudaMallocArray(&s.arr, &fmt, c->W, c->H, flags);
         if (e != cudaSuccess) {
             free_slots(c);
@@ -202,6 +218,16 @@ LaunchConfig launch_config(const rct_ctx *c, int kind) {
     return lc;
 }
 
+void init_params(const rct_ctx *c, BpParams *p) {
+    std::memset(p, 0, sizeof *p);
+    p->vol = c->vol;
+    p->L = c->L;
+    p->W = c->W;
+    p->H = c->H;
+    p->cen = 0.5f * (c->L - 1);
+    p->tex_zrun = tex_zrun_of(c);
+}
+
 // FP32 view parameters for one view and kernel kind, from the FP64 fold.
 void make_view(const rct_ctx *c, int view, int kind, ViewParams *vp) {
     const double *f = &c->fold[12 * (size_t)view];
@@ -237,11 +263,15 @@ cudaError_t launch(rct_ctx *c, const LaunchConfig &lc, const BpParams &p, cudaSt
     cudaError_t e;
     if (c->prof_on && (e = prof_event(c, s)) != cudaSuccess) return e;
     c->launches += 1;
-    switch (lc.gather) {
-        case G_LDG: e = launch_bp_ldg(lc, p, s); break;
-        case G_TLD4: e = launch_bp_tld4(lc, p, s); break;
-        case G_TEXLIN: e = launch_bp_texlin(lc, p, s); break;
-        default: e = cudaErrorInvalidValue;
+    if (lc.gather == G_TEXLIN) {
+        e = launch_bp_texlin(lc, p, s);
+    } else {
+        switch (lc.dtype) {
+            case DT_F32: e = launch_bp_soft_f32(lc, p, s); break;
+            case DT_F16: e = launch_bp_soft_f16(lc, p, s); break;
+            case DT_BF16: e = launch_bp_soft_bf16(lc, p, s); break;
+            default: e = cudaErrorInvalidValue;
+        }
     }
     if (e == cudaSuccess && c->prof_on) e = prof_event(c, s);
     return e;
@@ -270,12 +300,12 @@ rct_status stage_view(rct_ctx *c, Slot &slot, const void *src, bool from_host, c
 // batches in flight), linear staging for LDG input and for BF16 bound to a filtered texture.
 rct_status ensure_host_staging(rct_ctx *c) {
     rct_status st;
-    const int kind = effective_gather(c);
+    const int kind = kernel_kind(c);
     const int K = c->tune.views_per_pass;
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
     if ((st = ensure_copy_machinery(c))) return st;
-    if ((st = ensure_slots(c, kind, 2 * K))) return st;
-    const bool linear = (kind == G_LDG) || (kind == G_TEXLIN && c->dtype == DT_BF16);
+    if ((st = ensure_slots(c, 2 * K))) return st;
+    const bool linear = uses_linear(c);
     if (linear && c->lin_stage_bytes < 2 * K * view_bytes) {
         if (c->lin_stage) cudaFree(c->lin_stage);
         c->lin_stage = nullptr;
@@ -441,6 +471,7 @@ rct_status rct_set_tuning(rct_ctx *c, const rct_tuning *t) {
     if (t->block_x) n.block_x = t->block_x;
     if (t->block_y) n.block_y = t->block_y;
     if (t->gather) n.gather = t->gather;
+    if (t->tex_zrun) n.tex_zrun = t->tex_zrun;
     if (n.views_per_pass < 1 || n.views_per_pass > KMAX)
         return fail(RCT_EINVAL, "views_per_pass %d outside 1..%d", n.views_per_pass, KMAX);
     if (n.zrun != 1 && n.zrun != 2 && n.zrun != 4 && n.zrun != 8) return fail(RCT_EINVAL, "zrun %d not in {1,2,4,8}", n.zrun);
@@ -448,7 +479,8 @@ rct_status rct_set_tuning(rct_ctx *c, const rct_tuning *t) {
     if (c->L % n.xvec != 0) return fail(RCT_EINVAL, "xvec %d does not divide L = %d", n.xvec, c->L);
     if (n.block_x < 1 || n.block_y < 1 || n.block_x * n.block_y > 512 || (n.block_x * n.block_y) % 32 != 0)
         return fail(RCT_EINVAL, "block %dx%d: need a multiple of 32 threads, at most 512", n.block_x, n.block_y);
-    if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_TLD4) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
+    if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_MIX) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
+    if (n.tex_zrun < 0 || n.tex_zrun > 8) return fail(RCT_EINVAL, "tex_zrun %d outside 0..8", n.tex_zrun);
     c->tune = n;
     return RCT_OK;
 }
@@ -456,8 +488,8 @@ rct_status rct_set_tuning(rct_ctx *c, const rct_tuning *t) {
 rct_status rct_get_tuning(const rct_ctx *c, rct_tuning *out) {
     if (!c || !out) return fail(RCT_EINVAL, "null pointer");
     *out = c->tune;
-    const int g = effective_gather(c);
-    out->gather = (g == G_LDG) ? RCT_GATHER_LDG : RCT_GATHER_TLD4;
+    if (out->gather == RCT_GATHER_AUTO) out->gather = RCT_GATHER_TLD4;
+    out->tex_zrun = tex_zrun_of(c);
     return RCT_OK;
 }
 
@@ -482,32 +514,27 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
     if ((st = validate_range(c, d_proj, first_view, n))) return st;
     if (n == 0) return RCT_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int kind = effective_gather(c);
+    const int kind = kernel_kind(c);
     const int K = c->tune.views_per_pass;
-    if ((st = ensure_slots(c, kind, K))) return st;
+    const bool tex = uses_tex(c);
+    if ((st = ensure_slots(c, K))) return st;
     if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
     const LaunchConfig lc = launch_config(c, kind);
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
     const char *base = static_cast<const char *>(d_proj);
 
-    BpParams p{};
-    p.vol = c->vol;
-    p.L = c->L;
-    p.W = c->W;
-    p.H = c->H;
-    p.cen = 0.5f * (c->L - 1);
+    BpParams p;
+    init_params(c, &p);
     for (int b = 0; b < n; b += K) {
         const int kb = std::min(K, n - b);
         p.K = kb;
         p.accumulate = c->vol_zero_pending ? 0 : 1;
         for (int k = 0; k < kb; ++k) {
-            const int view = first_view + b + k;
             ViewParams &vp = p.view[k];
-            make_view(c, view, kind, &vp);
+            make_view(c, first_view + b + k, kind, &vp);
             const void *src = base + (size_t)(b + k) * view_bytes;
-            if (kind == G_LDG) {
-                vp.img = src;
-            } else {
+            vp.img = src;
+            if (tex) {
                 Slot &slot = c->slots[k];
                 if ((st = stage_view(c, slot, src, false, s))) return st;
                 vp.tex = slot.tex;
@@ -526,11 +553,12 @@ rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, 
     if ((st = validate_range(c, h_proj, first_view, n))) return st;
     if (n == 0) return RCT_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int kind = effective_gather(c);
+    const int kind = kernel_kind(c);
     const int K = c->tune.views_per_pass;
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
     if ((st = ensure_host_staging(c))) return st;
-    const bool linear = (kind == G_LDG) || (kind == G_TEXLIN && c->dtype == DT_BF16);
+    const bool tex = uses_tex(c);
+    const bool linear = uses_linear(c);
     const LaunchConfig lc = launch_config(c, kind);
     const char *base = static_cast<const char *>(h_proj);
 
@@ -539,46 +567,33 @@ rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, 
     RCT_CUDA(cudaEventRecord(c->ev_free[0], s), "cudaEventRecord");
     RCT_CUDA(cudaEventRecord(c->ev_free[1], s), "cudaEventRecord");
 
-    BpParams p{};
-    p.vol = c->vol;
-    p.L = c->L;
-    p.W = c->W;
-    p.H = c->H;
-    p.cen = 0.5f * (c->L - 1);
+    BpParams p;
+    init_params(c, &p);
     int batch = 0;
     for (int b = 0; b < n; b += K, ++batch) {
         const int g = batch & 1;
         const int kb = std::min(K, n - b);
         // copy stream: wait until group g's previous pass is done, then fill it
         RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[g], 0), "cudaStreamWaitEvent");
-        for (int k = 0; k < kb; ++k) {
-            const void *src = base + (size_t)(b + k) * view_bytes;
-            if (linear) {
-                char *dst = static_cast<char *>(c->lin_stage) + (size_t)(g * K + k) * view_bytes;
-                RCT_CUDA(cudaMemcpyAsync(dst, src, view_bytes, cudaMemcpyHostToDevice, c->copy_stream), "cudaMemcpyAsync");
-            } else {
-                if ((st = stage_view(c, c->slots[g * K + k], src, true, c->copy_stream))) return st;
-            }
-        }
-        RCT_CUDA(cudaEventRecord(c->ev_filled[g], c->copy_stream), "cudaEventRecord");
-        RCT_CUDA(cudaStreamWaitEvent(s, c->ev_filled[g], 0), "cudaStreamWaitEvent");
         p.K = kb;
         p.accumulate = c->vol_zero_pending ? 0 : 1;
         for (int k = 0; k < kb; ++k) {
-            const int view = first_view + b + k;
+            const void *src = base + (size_t)(b + k) * view_bytes;
             ViewParams &vp = p.view[k];
-            make_view(c, view, kind, &vp);
-            const char *lin = static_cast<const char *>(c->lin_stage) + (size_t)(g * K + k) * view_bytes;
-            if (kind == G_LDG) {
+            make_view(c, first_view + b + k, kind, &vp);
+            Slot *slot = tex ? &c->slots[g * K + k] : nullptr;
+            if (linear) {
+                char *lin = static_cast<char *>(c->lin_stage) + (size_t)(g * K + k) * view_bytes;
+                RCT_CUDA(cudaMemcpyAsync(lin, src, view_bytes, cudaMemcpyHostToDevice, c->copy_stream), "cudaMemcpyAsync");
+                if (slot && (st = stage_view(c, *slot, lin, false, c->copy_stream))) return st;
                 vp.img = lin;
-            } else {
-                Slot &slot = c->slots[g * K + k];
-                if (linear) {  // BF16 for a filtered texture: widen from the linear copy on `stream`
-                    if ((st = stage_view(c, slot, lin, false, s))) return st;
-                }
-                vp.tex = slot.tex;
+            } else if (slot) {
+                if ((st = stage_view(c, *slot, src, true, c->copy_stream))) return st;
             }
+            if (slot) vp.tex = slot->tex;
         }
+        RCT_CUDA(cudaEventRecord(c->ev_filled[g], c->copy_stream), "cudaEventRecord");
+        RCT_CUDA(cudaStreamWaitEvent(s, c->ev_filled[g], 0), "cudaStreamWaitEvent");
         cudaError_t e = launch(c, lc, p, s);
         if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
         c->vol_zero_pending = false;
@@ -635,9 +650,8 @@ int64_t rct_launch_count(const rct_ctx *c) { return c ? c->launches : -1; }
 rct_status rct_prepare(rct_ctx *c, int host_input) {
     rct_status st = check_ctx(c);
     if (st) return st;
-    const int kind = effective_gather(c);
-    if ((st = ensure_slots(c, kind, c->tune.views_per_pass))) return st;
-    if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
+    if ((st = ensure_slots(c, c->tune.views_per_pass))) return st;
+    if (kernel_kind(c) == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
     if (host_input && (st = ensure_host_staging(c))) return st;
     return RCT_OK;
 }

@@ -6,13 +6,23 @@
 // views of one pass, so the volume is read and written once per K views
 // (8/K bytes of HBM traffic per voxel update instead of the listing's 8).
 //
-// Per voxel update (Part 1): three FMAs give (u', v', w) from the folded
-// matrix, one approximate reciprocal r = 1/w (as the paper's kernels use a
-// reciprocal instead of a divide, Section "SIMD Vectorization"), two
-// multiplies give q = (u' r, v' r).  floor(q) and frac(q) come from one
-// directed-rounding add of 1.5 * 2^23 (the integer part lands in the low
-// mantissa bits), which keeps the conversion off the quarter-rate pipe.
-// Part 2 fetches the 2x2 cell, Part 3 does three lerps and adds val * r^2.
+// Part 1 per voxel update: the (u', v') pair comes from one packed FMA
+// (f32x2) and w from one FMA of the folded matrix; one approximate
+// reciprocal r = 1/w (the paper's kernels also use a reciprocal instead of a
+// divide, Section "SIMD Vectorization"); one packed multiply gives
+// q = (u' r, v' r).  floor(q) and frac(q) come from a packed add of
+// 1.5 * 2^23 rounded toward -inf (the integer part lands in the low mantissa
+// bits), so no conversion instruction is needed.
+//
+// Part 2 fetches the 2x2 cell by one of two routes, chosen per z position of
+// the run by a uniform run-time split (tex_zrun):
+//   * texture gather (tld4) from a staged gather-capable array with a zero
+//     border -- the texture pipe;
+//   * four predicated read-only global loads from the caller's linear image
+//     -- the load/store pipe.
+// Using both routes in one thread keeps both fetch units busy (a 2x2 gather
+// of 32-bit texels costs the texture unit two slots).
+// Part 3: three lerps and acc += val * r^2.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -45,54 +55,53 @@ __device__ __forceinline__ float load_px(const void *img, ptrdiff_t off) {
     }
 }
 
-// Part 2 + 3 for one voxel and one view: returns the bilinear value at
-// detector position (cu + qx, cv + qy), zero outside the W x H image.
-template <int G, int DT>
-__device__ __forceinline__ float sample(const ViewParams &v, float qx, float qy, int W, int H) {
-    if constexpr (G == G_TEXLIN) {
-        // Texture-unit bilinear; the matrix already carries the +0.5 texel-centre shift.
-        return tex2D<float>(static_cast<cudaTextureObject_t>(v.tex), qx, qy);
-    } else {
-        const float tx = __fadd_rd(qx, kMagic);   // kMagic + floor(qx)
-        const float ty = __fadd_rd(qy, kMagic);
-        const float flx = tx - kMagic;            // floor(qx), exact
-        const float fly = ty - kMagic;
-        const float fx = qx - flx;                // interpolation weights in [0, 1)
-        const float fy = qy - fly;
-        float a, b, c, d;                          // (i0,j0) (i0+1,j0) (i0,j0+1) (i0+1,j0+1)
-        if constexpr (G == G_TLD4) {
-            // The gather footprint of coordinate (i0 + 1, j0 + 1) is exactly texels i0..i0+1,
-            // j0..j0+1 (texel centres at +0.5), independent of the unit's coordinate rounding.
-            const float gx = tx - (kMagic - static_cast<float>(v.cu + 1));
-            const float gy = ty - (kMagic - static_cast<float>(v.cv + 1));
-            const cudaTextureObject_t t = static_cast<cudaTextureObject_t>(v.tex);
-            if constexpr (DT == DT_BF16) {
-                const uint4 g = tex2Dgather<uint4>(t, gx, gy, 0);
-                a = __uint_as_float(g.w << 16);
-                b = __uint_as_float(g.z << 16);
-                c = __uint_as_float(g.x << 16);
-                d = __uint_as_float(g.y << 16);
-            } else {
-                const float4 g = tex2Dgather<float4>(t, gx, gy, 0);
-                a = g.w; b = g.z; c = g.x; d = g.y;
-            }
+// Per-view constants the inner loop needs, hoisted out of the z-run.
+struct ViewConsts {
+    float2 m_z;      // (m[2], m[6]): step of (u', v') per z voxel
+    float w_z;       // m[10]
+    float2 gofs;     // -(kMagic - (cu + 1), kMagic - (cv + 1)): gather-corner offset
+    int cu, cv;
+    cudaTextureObject_t tex;
+    const void *img;
+};
+
+// Parts 2 + 3 for one voxel: bilinear value at detector (cu + q.x, cv + q.y), zero outside.
+template <int DT, bool TEXPATH>
+__device__ __forceinline__ float sample_soft(const ViewConsts &c, float2 q, int W, int H) {
+    const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));           // kMagic + floor(q)
+    const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));         // floor(q), exact
+    const float2 f = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), q);          // q - floor(q), exact
+    float a, b, cc, d;                                                      // (i0,j0) (i0+1,j0) (i0,j0+1) (i0+1,j0+1)
+    if constexpr (TEXPATH) {
+        // The gather footprint of coordinate (i0 + 1, j0 + 1) is exactly texels i0..i0+1 x
+        // j0..j0+1 (texel centres at +0.5), independent of the unit's coordinate rounding.
+        const float2 g = __fadd2_rn(t, c.gofs);
+        if constexpr (DT == DT_BF16) {
+            const uint4 v = tex2Dgather<uint4>(c.tex, g.x, g.y, 0);
+            a = __uint_as_float(v.w << 16);
+            b = __uint_as_float(v.z << 16);
+            cc = __uint_as_float(v.x << 16);
+            d = __uint_as_float(v.y << 16);
         } else {
-            const int i0 = __float_as_int(tx) - kMagicBits + v.cu;
-            const int j0 = __float_as_int(ty) - kMagicBits + v.cv;
-            const bool x0 = static_cast<unsigned>(i0) < static_cast<unsigned>(W);
-            const bool x1 = static_cast<unsigned>(i0 + 1) < static_cast<unsigned>(W);
-            const bool y0 = static_cast<unsigned>(j0) < static_cast<unsigned>(H);
-            const bool y1 = static_cast<unsigned>(j0 + 1) < static_cast<unsigned>(H);
-            const ptrdiff_t o = static_cast<ptrdiff_t>(j0) * W + i0;
-            a = (y0 && x0) ? load_px<DT>(v.img, o) : 0.0f;
-            b = (y0 && x1) ? load_px<DT>(v.img, o + 1) : 0.0f;
-            c = (y1 && x0) ? load_px<DT>(v.img, o + W) : 0.0f;
-            d = (y1 && x1) ? load_px<DT>(v.img, o + W + 1) : 0.0f;
+            const float4 v = tex2Dgather<float4>(c.tex, g.x, g.y, 0);
+            a = v.w; b = v.z; cc = v.x; d = v.y;
         }
-        const float t0 = fmaf(fx, b - a, a);
-        const float t1 = fmaf(fx, d - c, c);
-        return fmaf(fy, t1 - t0, t0);
+    } else {
+        const int i0 = __float_as_int(t.x) - kMagicBits + c.cu;
+        const int j0 = __float_as_int(t.y) - kMagicBits + c.cv;
+        const bool x0 = static_cast<unsigned>(i0) < static_cast<unsigned>(W);
+        const bool x1 = static_cast<unsigned>(i0 + 1) < static_cast<unsigned>(W);
+        const bool y0 = static_cast<unsigned>(j0) < static_cast<unsigned>(H);
+        const bool y1 = static_cast<unsigned>(j0 + 1) < static_cast<unsigned>(H);
+        const ptrdiff_t o = static_cast<ptrdiff_t>(j0) * W + i0;
+        a = (y0 && x0) ? load_px<DT>(c.img, o) : 0.0f;
+        b = (y0 && x1) ? load_px<DT>(c.img, o + 1) : 0.0f;
+        cc = (y1 && x0) ? load_px<DT>(c.img, o + W) : 0.0f;
+        d = (y1 && x1) ? load_px<DT>(c.img, o + W + 1) : 0.0f;
     }
+    const float t0 = fmaf(f.x, b - a, a);
+    const float t1 = fmaf(f.x, d - cc, cc);
+    return fmaf(f.y, t1 - t0, t0);
 }
 
 template <int G, int DT, int XV, int R>
@@ -125,27 +134,46 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
     const float xc0 = static_cast<float>(x0) - p.cen;
     const float yc = static_cast<float>(y) - p.cen;
     const float zc0 = static_cast<float>(z0) - p.cen;
+    const int tex_zrun = p.tex_zrun;   // z positions [0, tex_zrun) use the texture route
 
 #pragma unroll 1
     for (int k = 0; k < p.K; ++k) {
         const ViewParams &v = p.view[k];
         const float *m = v.m;
-        // Part 1 at the thread's first voxel, then steps along z and x.
-        const float bu = fmaf(m[0], xc0, fmaf(m[1], yc, fmaf(m[2], zc0, m[3])));
-        const float bv = fmaf(m[4], xc0, fmaf(m[5], yc, fmaf(m[6], zc0, m[7])));
+        // Part 1 at the thread's first voxel; (u', v') travel as one f32x2 pair.
+        const float2 buv = make_float2(fmaf(m[0], xc0, fmaf(m[1], yc, fmaf(m[2], zc0, m[3]))),
+                                       fmaf(m[4], xc0, fmaf(m[5], yc, fmaf(m[6], zc0, m[7]))));
         const float bw = fmaf(m[8], xc0, fmaf(m[9], yc, fmaf(m[10], zc0, m[11])));
+        ViewConsts c;
+        c.m_z = make_float2(m[2], m[6]);
+        c.w_z = m[10];
+        c.cu = v.cu;
+        c.cv = v.cv;
+        c.gofs = make_float2(-(kMagic - static_cast<float>(v.cu + 1)), -(kMagic - static_cast<float>(v.cv + 1)));
+        c.tex = static_cast<cudaTextureObject_t>(v.tex);
+        c.img = v.img;
+        const float2 m_x = make_float2(m[0], m[4]);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const float ur = fmaf(static_cast<float>(r), m[2], bu);
-            const float vr = fmaf(static_cast<float>(r), m[6], bv);
-            const float wr = fmaf(static_cast<float>(r), m[10], bw);
+            const float fr = static_cast<float>(r);
+            const float2 uvr = __ffma2_rn(make_float2(fr, fr), c.m_z, buv);
+            const float wr = fmaf(fr, c.w_z, bw);
 #pragma unroll
             for (int j = 0; j < XV; ++j) {
-                const float u = fmaf(static_cast<float>(j), m[0], ur);
-                const float vv = fmaf(static_cast<float>(j), m[4], vr);
-                const float w = fmaf(static_cast<float>(j), m[8], wr);
+                const float fj = static_cast<float>(j);
+                const float2 uv = (j == 0) ? uvr : __ffma2_rn(make_float2(fj, fj), m_x, uvr);
+                const float w = (j == 0) ? wr : fmaf(fj, m[8], wr);
                 const float rw = rcp_approx(w);
-                const float val = sample<G, DT>(v, u * rw, vv * rw, p.W, p.H);
+                const float2 q = __fmul2_rn(uv, make_float2(rw, rw));
+                float val;
+                if constexpr (G == G_TEXLIN) {
+                    // Texture-unit bilinear; the matrix already carries the +0.5 texel-centre shift.
+                    val = tex2D<float>(c.tex, q.x, q.y);
+                } else if (r < tex_zrun) {
+                    val = sample_soft<DT, true>(c, q, p.W, p.H);
+                } else {
+                    val = sample_soft<DT, false>(c, q, p.W, p.H);
+                }
                 acc[r][j] = fmaf(val, rw * rw, acc[r][j]);
             }
         }

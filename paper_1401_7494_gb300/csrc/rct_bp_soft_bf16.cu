@@ -1,0 +1,11 @@
+// Software-bilinear backprojection kernels, BF16 projections (texture-gather and/or
+// predicated-load route per z position; see rct_bp_kernel.cuh).
+#include "rct_bp_kernel.cuh"
+
+namespace rct {
+
+cudaError_t launch_bp_soft_bf16(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
+    return dispatch_xv<G_SOFT, DT_BF16>(c, p, s);
+}
+
+}  // namespace rct

@@ -1,0 +1,11 @@
+// Software-bilinear backprojection kernels, F32 projections (texture-gather and/or
+// predicated-load route per z position; see rct_bp_kernel.cuh).
+#include "rct_bp_kernel.cuh"
+
+namespace rct {
+
+cudaError_t launch_bp_soft_f32(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
+    return dispatch_xv<G_SOFT, DT_F32>(c, p, s);
+}
+
+}  // namespace rct

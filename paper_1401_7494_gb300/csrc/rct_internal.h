@@ -9,7 +9,9 @@ namespace rct {
 
 constexpr int KMAX = 32;  // views per pass held in the launch parameters
 
-enum Gather : int { G_LDG = 1, G_TLD4 = 2, G_TEXLIN = 3 };
+// G_SOFT: software bilinear; per z position of a run the 2x2 cell comes from a texture gather or
+// from predicated global loads (BpParams::tex_zrun).  G_TEXLIN: texture-unit bilinear.
+enum Gather : int { G_SOFT = 1, G_TEXLIN = 3 };
 enum DType : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 
 // One view as the kernel sees it.  The host folds the voxel origin, spacing
@@ -33,6 +35,7 @@ struct BpParams {
     int K;           // views in this pass, 1..KMAX
     float cen;       // (L - 1) / 2
     int accumulate;  // 0: the volume is logically zero, overwrite instead of adding
+    int tex_zrun;    // G_SOFT: z positions [0, tex_zrun) of each run use the texture gather
     ViewParams view[KMAX];
 };
 
@@ -45,10 +48,10 @@ struct LaunchConfig {
 };
 
 // Kernel launchers (one translation unit per gather kind).
-cudaError_t launch_bp_ldg(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
-cudaError_t launch_bp_tld4(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
+cudaError_t launch_bp_soft_f32(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
+cudaError_t launch_bp_soft_f16(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
+cudaError_t launch_bp_soft_bf16(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
 cudaError_t launch_bp_texlin(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
-bool bp_config_supported(const LaunchConfig &c);
 
 cudaError_t launch_convert(const float *src, void *dst, size_t n, int dtype, cudaStream_t s);
 cudaError_t launch_widen_bf16(const uint16_t *src, float *dst, size_t n, cudaStream_t s);

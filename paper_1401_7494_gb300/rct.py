@@ -20,7 +20,7 @@ from . import build as _build
 RCT_OK, RCT_EINVAL, RCT_ENOMEM, RCT_ECUDA, RCT_ESTATE, RCT_ETIMEOUT, RCT_ENOTSUP = range(7)
 RCT_PROJ_F32, RCT_PROJ_F16, RCT_PROJ_BF16 = 0, 1, 2
 RCT_INTERP_SOFT, RCT_INTERP_TEX = 0, 1
-RCT_GATHER_AUTO, RCT_GATHER_LDG, RCT_GATHER_TLD4 = 0, 1, 2
+RCT_GATHER_AUTO, RCT_GATHER_LDG, RCT_GATHER_TLD4, RCT_GATHER_MIX = 0, 1, 2, 3
 RCT_MAX_VIEWS_PER_PASS = 32
 STATUS_NAMES = {0: "RCT_OK", 1: "RCT_EINVAL", 2: "RCT_ENOMEM", 3: "RCT_ECUDA", 4: "RCT_ESTATE",
                 5: "RCT_ETIMEOUT", 6: "RCT_ENOTSUP"}
@@ -34,7 +34,8 @@ class RctError(RuntimeError):
 
 class rct_tuning(ctypes.Structure):
     _fields_ = [("views_per_pass", ctypes.c_int), ("zrun", ctypes.c_int), ("xvec", ctypes.c_int),
-                ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("gather", ctypes.c_int)]
+                ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("gather", ctypes.c_int),
+                ("tex_zrun", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -169,8 +170,8 @@ def rct_set_precision(ctx, proj_dtype: int, interp: int = RCT_INTERP_SOFT) -> No
     _check(lib().rct_set_precision(ctx, int(proj_dtype), int(interp)))
 
 
-def rct_set_tuning(ctx, views_per_pass=0, zrun=0, xvec=0, block_x=0, block_y=0, gather=0) -> None:
-    t = rct_tuning(views_per_pass, zrun, xvec, block_x, block_y, gather)
+def rct_set_tuning(ctx, views_per_pass=0, zrun=0, xvec=0, block_x=0, block_y=0, gather=0, tex_zrun=0) -> None:
+    t = rct_tuning(views_per_pass, zrun, xvec, block_x, block_y, gather, tex_zrun)
     _check(lib().rct_set_tuning(ctx, ctypes.byref(t)))
 
 

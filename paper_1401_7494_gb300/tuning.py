@@ -15,7 +15,7 @@ from . import rct
 
 CACHE = Path(os.environ.get("RCT_TUNING_CACHE", Path(__file__).resolve().parent / "tuning_cache.json"))
 
-DEFAULT = dict(views_per_pass=16, zrun=4, xvec=1, block_x=32, block_y=8, gather=rct.RCT_GATHER_TLD4)
+DEFAULT = dict(views_per_pass=16, zrun=4, xvec=1, block_x=32, block_y=8, gather=rct.RCT_GATHER_TLD4, tex_zrun=0)
 
 
 def _key(L: int, dtype: str, interp: str) -> str:

@@ -36,6 +36,8 @@ TUNINGS = [
     dict(gather=rct.RCT_GATHER_TLD4, views_per_pass=7, zrun=8, xvec=1, block_x=64, block_y=2),
     dict(gather=rct.RCT_GATHER_LDG, views_per_pass=32, zrun=1, xvec=1, block_x=32, block_y=4),
     dict(gather=rct.RCT_GATHER_TLD4, views_per_pass=3, zrun=2, xvec=2, block_x=16, block_y=16),
+    dict(gather=rct.RCT_GATHER_MIX, tex_zrun=2, views_per_pass=16, zrun=4, block_x=32, block_y=8),
+    dict(gather=rct.RCT_GATHER_MIX, tex_zrun=5, views_per_pass=9, zrun=8, xvec=2, block_x=16, block_y=8),
 ]
 
 
@@ -59,11 +61,11 @@ def test_fp32_parity_xvec4(small_cases, case):
 
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
-@pytest.mark.parametrize("gather", [rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG])
+@pytest.mark.parametrize("gather", [rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG, rct.RCT_GATHER_MIX])
 def test_reduced_precision_storage_parity(small_cases, dtype, gather):
     """FP16/BF16 storage: same parity bar against the oracle fed the rounded projections."""
     w, proj, host = small_cases["L40"]
-    got = gpu_backproject(w, proj, dtype=dtype, tuning=dict(gather=gather))
+    got = gpu_backproject(w, proj, dtype=dtype, tuning=dict(gather=gather, tex_zrun=2, zrun=4))
     assert_parity(got, oracle_volume(w, oracle_inputs(host, dtype)), f"{dtype} storage")
     # and the stated (not gated) error against the FP32-input oracle stays small
     rms, _ = rel_errors(got, oracle_volume(w, host))
@@ -127,8 +129,8 @@ def test_split_calls_and_checkpoint_resume(small_cases, cuda_device):
 
 def test_host_input_path_matches_device_path(small_cases):
     w, proj, host = small_cases["L40"]
-    for gather in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG):
-        tun = dict(views_per_pass=5, gather=gather)
+    for gather in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG, rct.RCT_GATHER_MIX):
+        tun = dict(views_per_pass=5, gather=gather, zrun=4, tex_zrun=1)
         dev = gpu_backproject(w, proj, tuning=tun)
         pinned = torch.from_numpy(host).pin_memory()
         stream = torch.cuda.current_stream()
@@ -179,7 +181,7 @@ def test_argument_errors(cuda_device):
         with pytest.raises(rct.RctError):
             rct.rct_backproject(bp.ctx, 0, 0, 2, None)
         for bad in [dict(views_per_pass=33), dict(zrun=3), dict(xvec=3), dict(block_x=7, block_y=1),
-                    dict(block_x=1024, block_y=1), dict(gather=9)]:
+                    dict(block_x=1024, block_y=1), dict(gather=9), dict(tex_zrun=9)]:
             with pytest.raises(rct.RctError):
                 bp.set_tuning(**bad)
         with pytest.raises(rct.RctError):
