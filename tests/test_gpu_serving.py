@@ -1,0 +1,78 @@
+"""Serving on the GPU: results are the same alone and in a concurrent mix, and match the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from paper_1401_7494_gb300 import serving
+from gpu_helpers import assert_parity, oracle_volume, oracle_inputs
+
+pytestmark = pytest.mark.gpu
+
+W, H = 160, 123
+
+
+@pytest.fixture(scope="module")
+def setup(cuda_device):
+    protos, host, works = {}, {}, {}
+    for name, n, seed in [("pA", 24, 51), ("pB", 40, 52)]:
+        w = synth.make_workload(32, n_views=n, det_w=W, det_h=H, seed=seed)
+        protos[name] = serving.Protocol_(name, W, H, w.geom.matrices)
+        p = w.projections(device=cuda_device)
+        host[name] = p.cpu().pin_memory()
+        works[name] = w
+    return protos, host, works
+
+
+def _req(rid, L, proto, n, arrival, mode="f32", interval=0.0):
+    sp = 256.0 / L
+    return serving.Request(rid, L, proto, n, arrival, mode, chunk_views=16, chunk_interval=interval,
+                           origin=(-(L - 1) / 2 * sp,) * 3, spacing=(sp,) * 3)
+
+
+def _serve(protos, host, reqs, graphs=True):
+    ex = serving.GpuExecutor(protos, host, use_graphs=graphs)
+    sch = serving.Scheduler(ex, 8 << 30, max_active=8, keep_volumes=True)
+    res = sch.run(reqs)
+    stats = (ex.captures, ex.graph_launches)
+    ex.close()
+    return res, stats
+
+
+@pytest.mark.parametrize("mode", ["f32", "f16"])
+def test_alone_equals_in_the_mix_and_matches_oracle(setup, mode):
+    protos, host, works = setup
+    target = _req(0, 37, "pB", 40, 0.0, mode)
+    alone, _ = _serve(protos, host, [target])
+    assert alone[0].status == "ok"
+    mix = [_req(0, 37, "pB", 40, 0.002, mode, interval=0.001)]
+    mix += [_req(i, L, p, n, 0.0005 * i, mode, interval=0.0007)
+            for i, (L, p, n) in enumerate([(24, "pA", 24), (48, "pB", 40), (37, "pB", 40), (24, "pA", 24),
+                                           (64, "pA", 24), (37, "pA", 24)], start=1)]
+    res, (captures, launches) = _serve(protos, host, mix)
+    assert all(r.status == "ok" for r in res)
+    assert torch.equal(res[0].volume, alone[0].volume), "result changed when served in a mix"
+    assert launches == sum(q.n_chunks for q in mix) and captures <= launches
+    # and it is a correct reconstruction
+    w = works["pB"]
+    w37 = synth.Workload("t", 37, w.geom, np.array(target.origin), np.array(target.spacing), w.phantom, w.seed)
+    ref = oracle_volume(w37, oracle_inputs(host["pB"].numpy(), "f16" if mode == "f16" else "f32"))
+    assert_parity(res[0].volume.numpy(), ref, f"served {mode}")
+
+
+def test_graph_and_direct_paths_agree(setup):
+    protos, host, _ = setup
+    reqs = [_req(0, 40, "pA", 24, 0.0), _req(1, 40, "pA", 24, 0.0)]
+    g, _ = _serve(protos, host, reqs, graphs=True)
+    d, _ = _serve(protos, host, reqs, graphs=False)
+    for a, b in zip(g, d):
+        assert torch.equal(a.volume, b.volume)
+
+
+def test_slots_and_graphs_are_reused_across_requests(setup):
+    protos, host, _ = setup
+    reqs = [_req(0, 40, "pB", 40, 0.0), _req(1, 40, "pB", 40, 0.5)]      # same shape, one after the other
+    res, (captures, launches) = _serve(protos, host, reqs)
+    assert [r.status for r in res] == ["ok", "ok"]
+    assert captures == reqs[0].n_chunks and launches == 2 * reqs[0].n_chunks
+    assert torch.equal(res[0].volume, res[1].volume)
