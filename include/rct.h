@@ -245,6 +245,33 @@ RCT_API rct_status rct_fold_geometry(int L, int n_views, const double *matrices,
 RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float step_px, int iters, double *rate);
 RCT_API rct_status rct_probe_update_stream(size_t bytes, double *rate);
 
+/*
+ * Allocation-free backprojection (the paper has no counterpart; it exists for
+ * callers that cannot allocate device memory: code running inside another
+ * framework that owns the memory pool, latency-critical loops where
+ * cudaMalloc/cudaFree would synchronise the device, pipelines with a memory
+ * budget fixed at start-up).  No context is needed and nothing is allocated:
+ * the n FP32 device images d_proj (H x W row-major, views in order) are
+ * narrowed to FP16 into a scratch array that is part of the loaded library
+ * (a fixed 32 MiB of device memory per GPU, held until the process exits)
+ * and backprojected with the FP16 predicated-load kernel into the caller's
+ * L^3 FP32 device volume d_volume (overwritten when accumulate == 0, added to
+ * otherwise).  matrices: n row-major 3x4 FP64 on the host; origin/spacing as
+ * in rct_set_geometry.  Views go through the scratch in batches of up to 32;
+ * one view must fit (det_w * det_h <= 16 Mi pixels), larger detectors give
+ * RCT_EINVAL.  The first call on a device looks up the scratch address with
+ * cudaGetSymbolAddress (make it before any stream capture); later calls only
+ * enqueue work on `stream`.  All calls on a device share the one scratch:
+ * calls whose work may overlap on the GPU (different streams without
+ * ordering) race on it and give wrong volumes; order them on one stream.
+ * Nothing in the scratch has to start at zero: each batch rewrites what it
+ * reads.  Same kernel as the context path with RCT_PROJ_F16 and
+ * RCT_GATHER_LDG, zrun 4, xvec 1, block 32x8.
+ */
+RCT_API rct_status rct_backproject_f16_noalloc(int L, int det_w, int det_h, const double *matrices, int n,
+                                               const double origin[3], const double spacing[3],
+                                               const float *d_proj, float *d_volume, int accumulate, void *stream);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 RCT_API const char *rct_last_error(void);
 

@@ -49,6 +49,16 @@ struct Slot {
 
 }  // namespace
 
+rct_status rct::rct_internal_fail(rct_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
 struct rct_ctx {
     int L = 0, W = 0, H = 0, n_views = 0;
     int device = 0;

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/rct.h"
+
 namespace rct {
 
 constexpr int KMAX = 32;  // views per pass held in the launch parameters
@@ -54,6 +56,9 @@ cudaError_t launch_bp_soft_bf16(const LaunchConfig &c, const BpParams &p, cudaSt
 cudaError_t launch_bp_texlin(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
 
 cudaError_t launch_convert(const float *src, void *dst, size_t n, int dtype, cudaStream_t s);
+
+// Record a message for rct_last_error() on the calling thread and return `code`.
+rct_status rct_internal_fail(rct_status code, const char *fmt, ...);
 cudaError_t launch_widen_bf16(const uint16_t *src, float *dst, size_t n, cudaStream_t s);
 
 }  // namespace rct

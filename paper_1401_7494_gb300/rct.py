@@ -74,6 +74,7 @@ SIGNATURES = {
     "rct_graph_destroy": (None, [_P]),
     "rct_probe_texture": (_I, [_I, _I, ctypes.c_float, ctypes.c_float, _I, ctypes.POINTER(ctypes.c_double)]),
     "rct_probe_update_stream": (_I, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]),
+    "rct_backproject_f16_noalloc": (_I, [_I, _I, _I, _D3, _I, _D3, _D3, _P, _P, _I, _P]),
     "rct_last_error": (ctypes.c_char_p, []),
     "rct_version": (_I, []),
 }
@@ -271,6 +272,18 @@ def rct_probe_update_stream(nbytes: int) -> float:
     r = ctypes.c_double()
     _check(lib().rct_probe_update_stream(nbytes, ctypes.byref(r)))
     return r.value
+
+
+def rct_backproject_f16_noalloc(L: int, det_w: int, det_h: int, matrices, origin, spacing, d_proj, n: int,
+                                d_volume, accumulate: bool = False, stream=None) -> None:
+    """Allocation-free FP16-storage backprojection into a caller-owned volume (see include/rct.h)."""
+    m = np.ascontiguousarray(np.asarray(matrices, dtype=np.float64).reshape(-1))
+    if m.size < 12 * n:
+        raise ValueError("matrices must hold 12 values per view")
+    o, po = _f64(origin, 3)
+    s, ps = _f64(spacing, 3)
+    _check(lib().rct_backproject_f16_noalloc(L, det_w, det_h, m.ctypes.data_as(_D3), n, po, ps, _addr(d_proj),
+                                             _addr(d_volume), 1 if accumulate else 0, _stream(stream)))
 
 
 def rct_fold_geometry(L: int, matrices, origin, spacing):
