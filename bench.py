@@ -43,6 +43,8 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true", help="skip the precision variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
     return ap.parse_args()
@@ -268,26 +270,37 @@ def run_ours(args, dist: Dist) -> dict | None:
     total_updates = dist.sum(float(w.updates * args.steps))
     value = total_updates / (max_ms / 1e3) / 1e9
 
-    # roofline of the dominant kernel (the backprojection pass)
+    # roofline of the dominant kernel (the backprojection pass).  The pass is bound by the L1TEX fetch
+    # path, not by HBM: its fetch ceilings are measured live with the library's probes, with the lane
+    # stride and z step of this workload (pixels per voxel at the isocentre).
     K = tun["views_per_pass"]
     n_launch = kernel_launches
     avg_kernel_s = kernel_ms / max(n_launch, 1) / 1e3
+    passes_per_step = -(-w.n_views // K)
+    upd_per_launch = w.updates / passes_per_step
+    kernel_gups = upd_per_launch / avg_kernel_s / 1e9
+    px_per_voxel = (w.geom.sdd / w.geom.sid) * float(w.spacing[0]) / w.geom.pitch
+    tex_peak = rct.rct_probe_texture(0, rct.RCT_PROJ_F32, px_per_voxel, px_per_voxel, 4096) / 1e9
+    ldg_peak = rct.rct_probe_texture(3, rct.RCT_PROJ_F32, px_per_voxel, px_per_voxel, 4096) / 1e9
+    route = {rct.RCT_GATHER_LDG: "ldg", rct.RCT_GATHER_MIX: "mix"}.get(tun.get("gather"), "tex")
+    fetch_peak = {"tex": tex_peak, "ldg": ldg_peak, "mix": tex_peak + ldg_peak}[route]
     vol_bytes = 4 * w.L ** 3
     img_bytes = 4 * w.geom.det_w * w.geom.det_h
-    passes_per_step = -(-w.n_views // K)
     # per step: the first pass writes only, later passes read and write; each view's image is read once
     bytes_per_step = vol_bytes * (1 + 2 * (passes_per_step - 1)) + img_bytes * w.n_views
     bytes_per_launch = bytes_per_step / passes_per_step
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved_gbs = bytes_per_launch / avg_kernel_s / 1e9
-    upd_per_launch = w.updates / passes_per_step
-    kernel_gups = upd_per_launch / avg_kernel_s / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None,
-                "kernel": "bp_kernel (backprojection pass)", "kernel_gups": round(kernel_gups, 2),
-                "kernel_share_of_step": round(kernel_ms / ms_total, 4),
-                "algorithmic_bytes_per_launch": int(bytes_per_launch), "updates_per_launch": int(upd_per_launch),
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    roofline = {"bound": "l1tex", "achieved": round(kernel_gups, 1), "peak": round(fetch_peak, 1),
+                "unit": "G cell-fetches/s (one 2x2 fetch per voxel update)",
+                "frac": round(kernel_gups / fetch_peak, 4), "traffic": None,
+                "kernel": f"bp_kernel, {route} route", "route": route,
+                "peak_source": f"measured live: tld4 FP32 gather probe {tex_peak:.1f} G/s + 4-load gather probe "
+                               f"{ldg_peak:.1f} G/s at lane stride {px_per_voxel:.2f} px",
+                "kernel_share_of_step": round(kernel_ms / ms_total, 4), "updates_per_launch": int(upd_per_launch),
+                "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(achieved_gbs / hbm_peak, 4), "algorithmic_bytes_per_launch": int(bytes_per_launch),
+                        "peak_source": "measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "fallback"}}
 
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
@@ -333,9 +346,8 @@ def run_ours(args, dist: Dist) -> dict | None:
         del pinned, vol_host
 
     bp.close()
-    host = None
+    host = proj.cpu().numpy() if dist.rank == 0 and not (args.no_variants and args.no_cpu_baseline) else None
     if dist.rank == 0 and not args.no_variants:
-        host = proj.cpu().numpy()
         L = w.L
         rng = np.random.default_rng(7)
         check_idx = np.unique(np.concatenate([rng.integers(0, L ** 3, size=8192),
@@ -343,16 +355,27 @@ def run_ours(args, dist: Dist) -> dict | None:
         import oracle
         variants = {}
         for dt, it in [("f32", "soft"), ("f16", "soft"), ("bf16", "soft"), ("f16", "tex"), ("f32", "tex")]:
-            ref_host = host if dt == "f32" else host   # error stated against the FP32-input FP64 oracle
+            # the error is stated against the FP64 oracle on the FP32 projections
             variants[f"{dt}_{it}"] = measure_variant(w, proj, dt, it, max(2, args.steps // 2), 1, stream,
-                                                     check_idx=check_idx, host=ref_host)
+                                                     check_idx=check_idx, host=host)
         result["variants"] = variants
         result["variants_note"] = ("GUPS per precision variant on the same workload; error vs the FP64 oracle on "
                                    f"FP32 projections over {check_idx.size} sampled voxels (a full z-plane + random)")
 
+    del proj
+    torch.cuda.empty_cache()
+    if dist.rank == 0 and not args.no_serve:
+        from paper_1401_7494_gb300 import serve_bench
+        protocols, host_data = serve_bench.build_protocols(dev)
+        served = {}
+        for mode in ("f32", "f16"):
+            served[mode] = serve_bench.run_mode(mode, protocols, host_data, n_requests=args.serve_requests,
+                                                log=lambda *_: None)
+        result["served"] = {m: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
+                            for m, r in served.items()}
+        del host_data
+
     if dist.rank == 0 and not args.no_cpu_baseline:
-        if host is None:
-            host = proj.cpu().numpy()
         gups, cores, sample = oracle_rate(w, host, args.cpu_seconds)
         result["cpu_baseline"] = {"value": round(gups, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                                   "sample": sample}

@@ -29,8 +29,10 @@
  *     stated otherwise; results are valid once the stream reaches them.
  *   - A context is bound to the CUDA device that is current when it is
  *     created; later calls must be made with that device current.  A context
- *     is not thread-safe; distinct contexts may be used from distinct threads
- *     and streams concurrently.
+ *     is not thread-safe, and the work of successive calls on one context
+ *     must be ordered (one stream, or streams the caller synchronises):
+ *     they share the context's staging buffers.  Distinct contexts may be
+ *     used from distinct threads and streams concurrently.
  *   - The library never falls back to a CPU computation.
  */
 #ifndef RCT_H
@@ -138,7 +140,10 @@ RCT_API rct_status rct_reset_volume(rct_ctx *ctx, void *stream);
 /*
  * Backproject views [first_view, first_view + n) into the volume, in view
  * order.  d_proj points to n device images (the first one belongs to view
- * first_view) in the element type set by rct_set_precision.  The caller
+ * first_view) in the element type set by rct_set_precision.  Texture routes
+ * stage each batch of K views into the context's gather arrays on an
+ * internal copy stream (forked from and joined back into `stream` with
+ * events), so staging overlaps the previous batch's pass.  The caller
  * owns d_proj and must keep it valid and unchanged until the stream reaches
  * the end of this call's work.  Asynchronous on `stream`; allocates nothing
  * once the context's staging buffers exist (they are created by the first
@@ -236,7 +241,8 @@ RCT_API rct_status rct_fold_geometry(int L, int n_views, const double *matrices,
  * Throughput probes (measurement support, allocate their own small buffers).
  * rct_probe_texture: fetches per second over the whole GPU for texture fetches
  * of one kind -- mode 0 = tld4 gather, 1 = point fetch, 2 = bilinear filtered
- * fetch -- from a 256x256 texture of dtype RCT_PROJ_F32 or RCT_PROJ_F16 that
+ * fetch, 3 = four predicated global loads of the 2x2 cell (FP32 only) --
+ * from a 256x256 texture (or linear image) of dtype RCT_PROJ_F32 or RCT_PROJ_F16 that
  * stays cache resident; neighbouring lanes sample stride_px apart along x and
  * each fetch advances step_px along y.  rct_probe_update_stream: bytes read +
  * written per second by a float4 read-modify-write sweep over `bytes` of

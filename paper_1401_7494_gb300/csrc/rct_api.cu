@@ -527,32 +527,48 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
     const int kind = kernel_kind(c);
     const int K = c->tune.views_per_pass;
     const bool tex = uses_tex(c);
-    if ((st = ensure_slots(c, K))) return st;
+    if (tex && (st = ensure_copy_machinery(c))) return st;
+    if ((st = ensure_slots(c, 2 * K))) return st;
     if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
     const LaunchConfig lc = launch_config(c, kind);
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
     const char *base = static_cast<const char *>(d_proj);
 
+    // Texture routes stage each batch into one of two slot groups on the copy stream, so the
+    // copies of batch b+1 overlap the pass of batch b.  Fork: the copy stream first waits for
+    // the work already queued on `stream`.
+    if (tex) {
+        RCT_CUDA(cudaEventRecord(c->ev_free[0], s), "cudaEventRecord");
+        RCT_CUDA(cudaEventRecord(c->ev_free[1], s), "cudaEventRecord");
+    }
     BpParams p;
     init_params(c, &p);
-    for (int b = 0; b < n; b += K) {
+    int batch = 0;
+    for (int b = 0; b < n; b += K, ++batch) {
+        const int g = batch & 1;
         const int kb = std::min(K, n - b);
         p.K = kb;
         p.accumulate = c->vol_zero_pending ? 0 : 1;
+        if (tex) RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[g], 0), "cudaStreamWaitEvent");
         for (int k = 0; k < kb; ++k) {
             ViewParams &vp = p.view[k];
             make_view(c, first_view + b + k, kind, &vp);
             const void *src = base + (size_t)(b + k) * view_bytes;
             vp.img = src;
             if (tex) {
-                Slot &slot = c->slots[k];
-                if ((st = stage_view(c, slot, src, false, s))) return st;
+                Slot &slot = c->slots[g * K + k];
+                if ((st = stage_view(c, slot, src, false, c->copy_stream))) return st;
                 vp.tex = slot.tex;
             }
+        }
+        if (tex) {
+            RCT_CUDA(cudaEventRecord(c->ev_filled[g], c->copy_stream), "cudaEventRecord");
+            RCT_CUDA(cudaStreamWaitEvent(s, c->ev_filled[g], 0), "cudaStreamWaitEvent");
         }
         cudaError_t e = launch(c, lc, p, s);
         if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
         c->vol_zero_pending = false;
+        if (tex) RCT_CUDA(cudaEventRecord(c->ev_free[g], s), "cudaEventRecord");
     }
     return RCT_OK;
 }
@@ -660,7 +676,8 @@ int64_t rct_launch_count(const rct_ctx *c) { return c ? c->launches : -1; }
 rct_status rct_prepare(rct_ctx *c, int host_input) {
     rct_status st = check_ctx(c);
     if (st) return st;
-    if ((st = ensure_slots(c, c->tune.views_per_pass))) return st;
+    if (uses_tex(c) && (st = ensure_copy_machinery(c))) return st;
+    if ((st = ensure_slots(c, 2 * c->tune.views_per_pass))) return st;
     if (kernel_kind(c) == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
     if (host_input && (st = ensure_host_staging(c))) return st;
     return RCT_OK;
@@ -671,7 +688,7 @@ size_t rct_footprint_bytes(int L, int det_w, int det_h, int proj_dtype, int view
     const size_t vol = (size_t)L * L * L * sizeof(float);
     const size_t px = (size_t)det_w * det_h;
     const size_t esz = dtype_size(proj_dtype);
-    const size_t slots = (size_t)(host_input ? 2 : 1) * views_per_pass;
+    const size_t slots = (size_t)2 * views_per_pass;                        // two batches in flight
     size_t bytes = vol + slots * px * (proj_dtype == DT_BF16 ? 4 : esz);   // BF16 may be widened for TEX
     if (host_input) bytes += 2 * (size_t)views_per_pass * px * esz;         // linear staging (worst case)
     return bytes;

@@ -104,7 +104,11 @@ __device__ __forceinline__ float sample_soft(const ViewConsts &c, float2 q, int 
     return fmaf(f.y, t1 - t0, t0);
 }
 
-template <int G, int DT, int XV, int R>
+// ROUTE (G_SOFT only): 0 = every z position by texture gather, 1 = every z position by
+// predicated loads, 2 = mixed by the run-time split p.tex_zrun.
+enum Route : int { ROUTE_TEX = 0, ROUTE_LDG = 1, ROUTE_MIX = 2 };
+
+template <int G, int DT, int XV, int R, int ROUTE>
 __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParams p) {
     const int L = p.L;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * XV;
@@ -169,6 +173,10 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
                 if constexpr (G == G_TEXLIN) {
                     // Texture-unit bilinear; the matrix already carries the +0.5 texel-centre shift.
                     val = tex2D<float>(c.tex, q.x, q.y);
+                } else if constexpr (ROUTE == ROUTE_TEX) {
+                    val = sample_soft<DT, true>(c, q, p.W, p.H);
+                } else if constexpr (ROUTE == ROUTE_LDG) {
+                    val = sample_soft<DT, false>(c, q, p.W, p.H);
                 } else if (r < tex_zrun) {
                     val = sample_soft<DT, true>(c, q, p.W, p.H);
                 } else {
@@ -193,31 +201,31 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
     }
 }
 
-template <int G, int DT, int XV, int R>
+template <int G, int DT, int XV, int R, int ROUTE>
 cudaError_t launch_one(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     const int gx = (p.L / XV + c.bx - 1) / c.bx;
     const dim3 grid(gx, (p.L + c.by - 1) / c.by, (p.L + R - 1) / R);
-    bp_kernel<G, DT, XV, R><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
+    bp_kernel<G, DT, XV, R, ROUTE><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
     return cudaGetLastError();
 }
 
-template <int G, int DT, int XV>
+template <int G, int DT, int XV, int ROUTE>
 cudaError_t dispatch_r(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     switch (c.zrun) {
-        case 1: return launch_one<G, DT, XV, 1>(c, p, s);
-        case 2: return launch_one<G, DT, XV, 2>(c, p, s);
-        case 4: return launch_one<G, DT, XV, 4>(c, p, s);
-        case 8: return launch_one<G, DT, XV, 8>(c, p, s);
+        case 1: return launch_one<G, DT, XV, 1, ROUTE>(c, p, s);
+        case 2: return launch_one<G, DT, XV, 2, ROUTE>(c, p, s);
+        case 4: return launch_one<G, DT, XV, 4, ROUTE>(c, p, s);
+        case 8: return launch_one<G, DT, XV, 8, ROUTE>(c, p, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <int G, int DT>
+template <int G, int DT, int ROUTE>
 cudaError_t dispatch_xv(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     switch (c.xv) {
-        case 1: return dispatch_r<G, DT, 1>(c, p, s);
-        case 2: return dispatch_r<G, DT, 2>(c, p, s);
-        case 4: return dispatch_r<G, DT, 4>(c, p, s);
+        case 1: return dispatch_r<G, DT, 1, ROUTE>(c, p, s);
+        case 2: return dispatch_r<G, DT, 2, ROUTE>(c, p, s);
+        case 4: return dispatch_r<G, DT, 4, ROUTE>(c, p, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -6,7 +6,7 @@
 namespace rct {
 
 cudaError_t launch_bp_texlin(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
-    return dispatch_xv<G_TEXLIN, DT_F32>(c, p, s);
+    return dispatch_xv<G_TEXLIN, DT_F32, ROUTE_TEX>(c, p, s);
 }
 
 }  // namespace rct

@@ -43,6 +43,30 @@ __global__ void __launch_bounds__(256) tex_probe_kernel(cudaTextureObject_t tex,
     if (acc == 1.2345e-30f) sink[0] = acc;
 }
 
+// Four predicated read-only loads of a 2x2 cell from a cache-resident linear image, the
+// load/store route of the backprojection kernel; same lane layout as tex_probe_kernel.
+__global__ void __launch_bounds__(256) ldg4_probe_kernel(const float *__restrict__ img, int iters, float stride,
+                                                         float step, float *sink) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    float x = 8.0f + lane * stride + (warp & 7) * 3.0f;
+    float y = 8.0f + ((warp >> 3) & 63) * 2.0f;
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+        const int i0 = __float2int_rd(x), j0 = __float2int_rd(y);
+        const bool ok = static_cast<unsigned>(i0) < static_cast<unsigned>(kTexSide - 1) &&
+                        static_cast<unsigned>(j0) < static_cast<unsigned>(kTexSide - 1);
+        const float *r0 = img + j0 * kTexSide + i0;
+        const float a = ok ? __ldg(r0) : 0.f, b = ok ? __ldg(r0 + 1) : 0.f;
+        const float c = ok ? __ldg(r0 + kTexSide) : 0.f, d = ok ? __ldg(r0 + kTexSide + 1) : 0.f;
+        acc += (a + b) + (c + d);
+        y += step;
+        y = (y > kTexSide - 16.0f) ? y - (kTexSide - 32.0f) : y;
+    }
+    if (acc == 1.2345e-30f) sink[0] = acc;
+}
+
 __global__ void update_stream_kernel(float4 *__restrict__ a, size_t n4, float s) {
     const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
     for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
@@ -56,13 +80,15 @@ __global__ void update_stream_kernel(float4 *__restrict__ a, size_t n4, float s)
 
 extern "C" {
 
-// mode: 0 = tld4 gather (point texture), 1 = point fetch, 2 = bilinear filtered fetch.
+// mode: 0 = tld4 gather (point texture), 1 = point fetch, 2 = bilinear filtered fetch,
+// 3 = four predicated global loads of the 2x2 cell (FP32 only; the load/store route).
 // dtype: RCT_PROJ_F32 or RCT_PROJ_F16 texels.  stride_px: x distance between neighbouring lanes,
 // step_px: y advance per fetch.  Writes fetches per second (whole GPU) to *rate.
 RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float step_px, int iters,
                                      double *rate) {
-    if (!rate || mode < 0 || mode > 2 || iters <= 0 || (dtype != RCT_PROJ_F32 && dtype != RCT_PROJ_F16))
+    if (!rate || mode < 0 || mode > 3 || iters <= 0 || (dtype != RCT_PROJ_F32 && dtype != RCT_PROJ_F16))
         return RCT_EINVAL;
+    if (mode == 3 && dtype != RCT_PROJ_F32) return RCT_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RCT_ECUDA;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -75,7 +101,8 @@ RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float
     rct_status st = RCT_ECUDA;
     do {
         if (cudaMallocArray(&arr, &fmt, kTexSide, kTexSide, mode == 0 ? cudaArrayTextureGather : 0) != cudaSuccess) break;
-        if (cudaMalloc(&sink, sizeof(float)) != cudaSuccess) break;
+        if (cudaMalloc(&sink, sizeof(float) * (1 + kTexSide * kTexSide)) != cudaSuccess) break;
+        if (cudaMemset(sink, 0, sizeof(float) * (1 + kTexSide * kTexSide)) != cudaSuccess) break;
         cudaResourceDesc rd{};
         rd.resType = cudaResourceTypeArray;
         rd.res.array.array = arr;
@@ -87,7 +114,8 @@ RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) break;
         const int block = 256, grid = sms * 8;
         auto run = [&]() {
-            if (mode == 0) tex_probe_kernel<0><<<grid, block>>>(tex, iters, stride_px, step_px, sink);
+            if (mode == 3) ldg4_probe_kernel<<<grid, block>>>(sink + 1, iters, stride_px, step_px, sink);
+            else if (mode == 0) tex_probe_kernel<0><<<grid, block>>>(tex, iters, stride_px, step_px, sink);
             else if (mode == 1) tex_probe_kernel<1><<<grid, block>>>(tex, iters, stride_px, step_px, sink);
             else tex_probe_kernel<2><<<grid, block>>>(tex, iters, stride_px, step_px, sink);
         };
