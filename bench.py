@@ -53,14 +53,22 @@ def parse_args():
 # ----------------------------------------------------------------------------- distributed plumbing
 
 class Dist:
-    def __init__(self, want: int):
+    """Replica bookkeeping for N > 1: every rank reconstructs its own volume on its own GPU (the
+    voxels are independent, so no data-path collective exists); ranks only meet at barriers and to
+    take the max of the timed region and the sum of the work done."""
+
+    def __init__(self, want: int, backend: str | None = None):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
+        self.device = "cpu"
         if self.world > 1:
+            import torch
             import torch.distributed as dist
-            dist.init_process_group("nccl")
+            backend = backend or ("nccl" if torch.cuda.is_available() else "gloo")
+            self.device = f"cuda:{self.local}" if backend == "nccl" else "cpu"
+            dist.init_process_group(backend)
             self.pg = dist
         if want != self.world and self.rank == 0:
             print(f"note: --gpus {want} but WORLD_SIZE={self.world}", file=sys.stderr)
@@ -69,21 +77,17 @@ class Dist:
         if self.pg:
             self.pg.barrier()
 
-    def max(self, x: float) -> float:
-        if not self.pg:
-            return x
+    def _reduce(self, x: float, op) -> float:
         import torch
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.pg.all_reduce(t, op=op)
         return float(t.item())
 
+    def max(self, x: float) -> float:
+        return self._reduce(x, self.pg.ReduceOp.MAX) if self.pg else x
+
     def sum(self, x: float) -> float:
-        if not self.pg:
-            return x
-        import torch
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
-        return float(t.item())
+        return self._reduce(x, self.pg.ReduceOp.SUM) if self.pg else x
 
     def close(self):
         if self.pg:

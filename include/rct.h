@@ -81,8 +81,10 @@ typedef enum rct_gather {
     RCT_GATHER_AUTO = 0,  /* let the library (or the tuning cache) choose */
     RCT_GATHER_LDG = 1,   /* four predicated read-only loads from the caller's linear images */
     RCT_GATHER_TLD4 = 2,  /* one texture gather (tld4) of the 2x2 cell from a staged copy */
-    RCT_GATHER_MIX = 3    /* per z-run: the first tex_zrun positions by tld4, the rest by loads, so the
-                             texture and load/store pipes work side by side */
+    RCT_GATHER_MIX = 3,   /* per z-run: the first tex_zrun positions by tld4, the rest by quad loads
+                             (below), so the texture and load/store pipes work side by side */
+    RCT_GATHER_QUAD = 4   /* one 128-bit load (64-bit for 16-bit data) of a staged, zero-padded "quad"
+                             copy of the image whose every element holds a whole 2x2 cell */
 } rct_gather;
 
 /* Kernel tuning.  Zero in any field means "keep the current value". */

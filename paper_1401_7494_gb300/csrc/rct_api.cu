@@ -79,6 +79,10 @@ struct rct_ctx {
     int slot_kind = -1;             // kernel gather kind the slots serve
     int slot_dtype = -1;
 
+    // quad staging (quad-load route): 2K zero-padded quad images
+    void *quad_buf = nullptr;
+    size_t quad_alloc = 0;
+
     // host-input path: linear device staging (LDG) and the copy stream
     void *lin_stage = nullptr;
     size_t lin_stage_bytes = 0;
@@ -100,12 +104,13 @@ namespace {
 
 int kernel_kind(const rct_ctx *c) { return c->interp == RCT_INTERP_TEX ? G_TEXLIN : G_SOFT; }
 
-// Number of z positions of each run that fetch through the texture gather (the rest load
-// from the linear image).  LDG: none; TLD4 (and AUTO): all; MIX: the tuned split.
+// Number of z positions of each run that fetch through the texture gather (the rest load).
+// LDG, QUAD: none; TLD4 (and AUTO): all; MIX: the tuned split.
 int tex_zrun_of(const rct_ctx *c) {
     const int R = c->tune.zrun;
     switch (c->tune.gather) {
-        case RCT_GATHER_LDG: return 0;
+        case RCT_GATHER_LDG:
+        case RCT_GATHER_QUAD: return 0;
         case RCT_GATHER_MIX: return R <= 1 ? R : std::min(std::max(c->tune.tex_zrun, 1), R - 1);
         default: return R;
     }
@@ -113,11 +118,23 @@ int tex_zrun_of(const rct_ctx *c) {
 
 bool uses_tex(const rct_ctx *c) { return kernel_kind(c) == G_TEXLIN || tex_zrun_of(c) > 0; }
 
-// The kernel reads the linear image (LDG route), or BF16 must be widened before a filtered texture.
+// The load part of the software route reads staged quad elements (QUAD, MIX).
+bool uses_quad(const rct_ctx *c) {
+    return kernel_kind(c) == G_SOFT && c->tune.gather != RCT_GATHER_LDG && tex_zrun_of(c) < c->tune.zrun;
+}
+
+// The kernel reads the caller's linear image (LDG route), or BF16 must be widened before a
+// filtered texture.
 bool uses_linear(const rct_ctx *c) {
     if (kernel_kind(c) == G_TEXLIN) return c->dtype == DT_BF16;
-    return tex_zrun_of(c) < c->tune.zrun;
+    return c->tune.gather == RCT_GATHER_LDG;
 }
+
+// Host input must land in linear device memory first when a kernel or a staging step reads it there.
+bool host_needs_linear(const rct_ctx *c) { return uses_linear(c) || uses_quad(c); }
+
+constexpr float kHostMagic = 12582912.0f;   // 1.5 * 2^23, the kernel's floor constant
+constexpr int kHostMagicBits = 0x4B400000;
 
 rct_tuning default_tuning(int L) {
     rct_tuning t{};
@@ -206,6 +223,23 @@ rct_status ensure_copy_machinery(rct_ctx *c) {
     return RCT_OK;
 }
 
+rct_status ensure_quads(rct_ctx *c, int n_slots) {
+    if (!uses_quad(c)) return RCT_OK;
+    const size_t need = (size_t)n_slots * quad_bytes(c->W, c->H, c->dtype);
+    if (c->quad_alloc >= need) return RCT_OK;
+    if (c->quad_buf) cudaFree(c->quad_buf);
+    c->quad_buf = nullptr;
+    c->quad_alloc = 0;
+    cudaError_t e = cudaMalloc(&c->quad_buf, need);
+    if (e != cudaSuccess) return fail(RCT_ENOMEM, "quad staging allocation of %zu bytes failed", need);
+    c->quad_alloc = need;
+    return RCT_OK;
+}
+
+void *quad_slot(const rct_ctx *c, int slot) {
+    return static_cast<char *>(c->quad_buf) + (size_t)slot * quad_bytes(c->W, c->H, c->dtype);
+}
+
 rct_status ensure_widen(rct_ctx *c, size_t elems) {
     if (c->widen_elems >= elems) return RCT_OK;
     if (c->widen_buf) cudaFree(c->widen_buf);
@@ -236,6 +270,7 @@ void init_params(const rct_ctx *c, BpParams *p) {
     p->H = c->H;
     p->cen = 0.5f * (c->L - 1);
     p->tex_zrun = tex_zrun_of(c);
+    p->quad = uses_quad(c) ? 1 : 0;
 }
 
 // FP32 view parameters for one view and kernel kind, from the FP64 fold.
@@ -255,8 +290,13 @@ void make_view(const rct_ctx *c, int view, int kind, ViewParams *vp) {
     for (int k = 0; k < 12; ++k) vp->m[k] = static_cast<float>(m[k]);
     vp->cu = cu;
     vp->cv = cv;
+    vp->gofs_x = -(kHostMagic - static_cast<float>(cu + 1));
+    vp->gofs_y = -(kHostMagic - static_cast<float>(cv + 1));
+    vp->qcx = kHostMagicBits - cu - 1;
+    vp->qcy = kHostMagicBits - cv - 1;
     vp->tex = 0;
     vp->img = nullptr;
+    vp->quad = nullptr;
 }
 
 cudaError_t prof_event(rct_ctx *c, cudaStream_t s) {
@@ -315,7 +355,8 @@ rct_status ensure_host_staging(rct_ctx *c) {
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
     if ((st = ensure_copy_machinery(c))) return st;
     if ((st = ensure_slots(c, 2 * K))) return st;
-    const bool linear = uses_linear(c);
+    if ((st = ensure_quads(c, 2 * K))) return st;
+    const bool linear = host_needs_linear(c);
     if (linear && c->lin_stage_bytes < 2 * K * view_bytes) {
         if (c->lin_stage) cudaFree(c->lin_stage);
         c->lin_stage = nullptr;
@@ -439,6 +480,7 @@ void rct_destroy(rct_ctx *c) {
     free_slots(c);
     if (c->vol) cudaFree(c->vol);
     if (c->lin_stage) cudaFree(c->lin_stage);
+    if (c->quad_buf) cudaFree(c->quad_buf);
     if (c->widen_buf) cudaFree(c->widen_buf);
     for (int i = 0; i < 2; ++i) {
         if (c->ev_filled[i]) cudaEventDestroy(c->ev_filled[i]);
@@ -489,7 +531,7 @@ rct_status rct_set_tuning(rct_ctx *c, const rct_tuning *t) {
     if (c->L % n.xvec != 0) return fail(RCT_EINVAL, "xvec %d does not divide L = %d", n.xvec, c->L);
     if (n.block_x < 1 || n.block_y < 1 || n.block_x * n.block_y > 512 || (n.block_x * n.block_y) % 32 != 0)
         return fail(RCT_EINVAL, "block %dx%d: need a multiple of 32 threads, at most 512", n.block_x, n.block_y);
-    if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_MIX) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
+    if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_QUAD) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
     if (n.tex_zrun < 0 || n.tex_zrun > 8) return fail(RCT_EINVAL, "tex_zrun %d outside 0..8", n.tex_zrun);
     c->tune = n;
     return RCT_OK;
@@ -527,17 +569,20 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
     const int kind = kernel_kind(c);
     const int K = c->tune.views_per_pass;
     const bool tex = uses_tex(c);
-    if (tex && (st = ensure_copy_machinery(c))) return st;
+    const bool quad = uses_quad(c);
+    const bool staged = tex || quad;
+    if (staged && (st = ensure_copy_machinery(c))) return st;
     if ((st = ensure_slots(c, 2 * K))) return st;
+    if ((st = ensure_quads(c, 2 * K))) return st;
     if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
     const LaunchConfig lc = launch_config(c, kind);
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
     const char *base = static_cast<const char *>(d_proj);
 
-    // Texture routes stage each batch into one of two slot groups on the copy stream, so the
-    // copies of batch b+1 overlap the pass of batch b.  Fork: the copy stream first waits for
-    // the work already queued on `stream`.
-    if (tex) {
+    // Staged routes (texture arrays, quad images) stage each batch into one of two slot groups
+    // on the copy stream, so the staging of batch b+1 overlaps the pass of batch b.  Fork: the
+    // copy stream first waits for the work already queued on `stream`.
+    if (staged) {
         RCT_CUDA(cudaEventRecord(c->ev_free[0], s), "cudaEventRecord");
         RCT_CUDA(cudaEventRecord(c->ev_free[1], s), "cudaEventRecord");
     }
@@ -549,7 +594,7 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
         const int kb = std::min(K, n - b);
         p.K = kb;
         p.accumulate = c->vol_zero_pending ? 0 : 1;
-        if (tex) RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[g], 0), "cudaStreamWaitEvent");
+        if (staged) RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[g], 0), "cudaStreamWaitEvent");
         for (int k = 0; k < kb; ++k) {
             ViewParams &vp = p.view[k];
             make_view(c, first_view + b + k, kind, &vp);
@@ -560,15 +605,20 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
                 if ((st = stage_view(c, slot, src, false, c->copy_stream))) return st;
                 vp.tex = slot.tex;
             }
+            if (quad) {
+                vp.quad = quad_slot(c, g * K + k);
+                cudaError_t e = launch_stage_quads(src, const_cast<void *>(vp.quad), c->W, c->H, c->dtype, c->copy_stream);
+                if (e != cudaSuccess) return cuda_fail(e, "quad staging kernel");
+            }
         }
-        if (tex) {
+        if (staged) {
             RCT_CUDA(cudaEventRecord(c->ev_filled[g], c->copy_stream), "cudaEventRecord");
             RCT_CUDA(cudaStreamWaitEvent(s, c->ev_filled[g], 0), "cudaStreamWaitEvent");
         }
         cudaError_t e = launch(c, lc, p, s);
         if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
         c->vol_zero_pending = false;
-        if (tex) RCT_CUDA(cudaEventRecord(c->ev_free[g], s), "cudaEventRecord");
+        if (staged) RCT_CUDA(cudaEventRecord(c->ev_free[g], s), "cudaEventRecord");
     }
     return RCT_OK;
 }
@@ -584,7 +634,8 @@ rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, 
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
     if ((st = ensure_host_staging(c))) return st;
     const bool tex = uses_tex(c);
-    const bool linear = uses_linear(c);
+    const bool quad = uses_quad(c);
+    const bool linear = host_needs_linear(c);
     const LaunchConfig lc = launch_config(c, kind);
     const char *base = static_cast<const char *>(h_proj);
 
@@ -612,6 +663,11 @@ rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, 
                 char *lin = static_cast<char *>(c->lin_stage) + (size_t)(g * K + k) * view_bytes;
                 RCT_CUDA(cudaMemcpyAsync(lin, src, view_bytes, cudaMemcpyHostToDevice, c->copy_stream), "cudaMemcpyAsync");
                 if (slot && (st = stage_view(c, *slot, lin, false, c->copy_stream))) return st;
+                if (quad) {
+                    vp.quad = quad_slot(c, g * K + k);
+                    cudaError_t e = launch_stage_quads(lin, const_cast<void *>(vp.quad), c->W, c->H, c->dtype, c->copy_stream);
+                    if (e != cudaSuccess) return cuda_fail(e, "quad staging kernel");
+                }
                 vp.img = lin;
             } else if (slot) {
                 if ((st = stage_view(c, *slot, src, true, c->copy_stream))) return st;
@@ -676,8 +732,9 @@ int64_t rct_launch_count(const rct_ctx *c) { return c ? c->launches : -1; }
 rct_status rct_prepare(rct_ctx *c, int host_input) {
     rct_status st = check_ctx(c);
     if (st) return st;
-    if (uses_tex(c) && (st = ensure_copy_machinery(c))) return st;
+    if ((uses_tex(c) || uses_quad(c)) && (st = ensure_copy_machinery(c))) return st;
     if ((st = ensure_slots(c, 2 * c->tune.views_per_pass))) return st;
+    if ((st = ensure_quads(c, 2 * c->tune.views_per_pass))) return st;
     if (kernel_kind(c) == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
     if (host_input && (st = ensure_host_staging(c))) return st;
     return RCT_OK;
@@ -690,6 +747,7 @@ size_t rct_footprint_bytes(int L, int det_w, int det_h, int proj_dtype, int view
     const size_t esz = dtype_size(proj_dtype);
     const size_t slots = (size_t)2 * views_per_pass;                        // two batches in flight
     size_t bytes = vol + slots * px * (proj_dtype == DT_BF16 ? 4 : esz);   // BF16 may be widened for TEX
+    bytes += slots * quad_bytes(det_w, det_h, proj_dtype);                    // quad staging (worst case)
     if (host_input) bytes += 2 * (size_t)views_per_pass * px * esz;         // linear staging (worst case)
     return bytes;
 }

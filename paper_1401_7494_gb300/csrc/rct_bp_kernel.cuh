@@ -14,15 +14,21 @@
 // 1.5 * 2^23 rounded toward -inf (the integer part lands in the low mantissa
 // bits), so no conversion instruction is needed.
 //
-// Part 2 fetches the 2x2 cell by one of two routes, chosen per z position of
-// the run by a uniform run-time split (tex_zrun):
+// Part 2 fetches the 2x2 cell by one of three routes (ROUTE below):
 //   * texture gather (tld4) from a staged gather-capable array with a zero
 //     border -- the texture pipe;
-//   * four predicated read-only global loads from the caller's linear image
-//     -- the load/store pipe.
-// Using both routes in one thread keeps both fetch units busy (a 2x2 gather
-// of 32-bit texels costs the texture unit two slots).
-// Part 3: three lerps and acc += val * r^2.
+//   * one 128-bit (64-bit for 16-bit data) load of a staged "quad" element
+//     that holds the whole cell, from a zero-padded copy of the image (the
+//     paper's zero-padded projection buffer, Section "SIMD Vectorization",
+//     taken one step further) -- the load/store pipe;
+//   * four predicated loads straight from the caller's linear image (no
+//     staging at all).
+// The mixed route splits each z-run between the texture gather and the quad
+// load, so both fetch units work side by side (a 2x2 gather of 32-bit texels
+// costs the texture unit two slots).
+// Cells whose four taps are all off the detector are skipped before any fetch.
+// Part 3: three lerps (two of them as one packed f32x2 pair for quads) and
+// acc += val * r^2.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -59,54 +65,106 @@ __device__ __forceinline__ float load_px(const void *img, ptrdiff_t off) {
 struct ViewConsts {
     float2 m_z;      // (m[2], m[6]): step of (u', v') per z voxel
     float w_z;       // m[10]
-    float2 gofs;     // -(kMagic - (cu + 1), kMagic - (cv + 1)): gather-corner offset
+    float2 gofs;     // t + gofs = gather corner (i0 + 1, j0 + 1)
     int cu, cv;
+    int qcx, qcy;    // bits(t) - qc = padded quad index (i0 + 1, j0 + 1)
     cudaTextureObject_t tex;
     const void *img;
+    const void *quad;
 };
 
-// Parts 2 + 3 for one voxel: bilinear value at detector (cu + q.x, cv + q.y), zero outside.
-template <int DT, bool TEXPATH>
-__device__ __forceinline__ float sample_soft(const ViewConsts &c, float2 q, int W, int H) {
+// Route of the load part of a z-run (G_SOFT only).
+//   ROUTE_TEX: every z position by texture gather;  ROUTE_LDG: every z position by four
+//   predicated loads from the linear image;  ROUTE_QLD: every z position by one quad load;
+//   ROUTE_MIX: z positions [0, tex_zrun) by texture gather, the rest by quad loads.
+enum Route : int { ROUTE_TEX = 0, ROUTE_LDG = 1, ROUTE_QLD = 2, ROUTE_MIX = 3 };
+
+// Part 2 + 3 by texture gather: adds the bilinear value at detector (cu + q.x, cv + q.y), times
+// w2, to acc.  A cell whose four taps are all off the detector contributes zero and is skipped
+// before the fetch (the clipping of the paper's Section "Implementation", done per voxel).
+template <int DT>
+__device__ __forceinline__ void accumulate_tex(const ViewConsts &c, float2 q, float w2, int W, int H, float &acc) {
     const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));           // kMagic + floor(q)
+    // padded cell index (i0 + 1, j0 + 1): in [0, W] x [0, H] iff some tap is on the image
+    const int ix = __float_as_int(t.x) - c.qcx;
+    const int jy = __float_as_int(t.y) - c.qcy;
+    if (static_cast<unsigned>(ix) > static_cast<unsigned>(W) || static_cast<unsigned>(jy) > static_cast<unsigned>(H))
+        return;
+    // The gather footprint of coordinate (i0 + 1, j0 + 1) is exactly texels i0..i0+1 x
+    // j0..j0+1 (texel centres at +0.5), independent of the unit's coordinate rounding.
+    const float2 g = __fadd2_rn(t, c.gofs);
+    float a, b, cc, d;                                                      // (i0,j0) (i0+1,j0) (i0,j0+1) (i0+1,j0+1)
+    if constexpr (DT == DT_BF16) {
+        const uint4 v = tex2Dgather<uint4>(c.tex, g.x, g.y, 0);
+        a = __uint_as_float(v.w << 16);
+        b = __uint_as_float(v.z << 16);
+        cc = __uint_as_float(v.x << 16);
+        d = __uint_as_float(v.y << 16);
+    } else {
+        const float4 v = tex2Dgather<float4>(c.tex, g.x, g.y, 0);
+        a = v.w; b = v.z; cc = v.x; d = v.y;
+    }
     const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));         // floor(q), exact
     const float2 f = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), q);          // q - floor(q), exact
-    float a, b, cc, d;                                                      // (i0,j0) (i0+1,j0) (i0,j0+1) (i0+1,j0+1)
-    if constexpr (TEXPATH) {
-        // The gather footprint of coordinate (i0 + 1, j0 + 1) is exactly texels i0..i0+1 x
-        // j0..j0+1 (texel centres at +0.5), independent of the unit's coordinate rounding.
-        const float2 g = __fadd2_rn(t, c.gofs);
-        if constexpr (DT == DT_BF16) {
-            const uint4 v = tex2Dgather<uint4>(c.tex, g.x, g.y, 0);
-            a = __uint_as_float(v.w << 16);
-            b = __uint_as_float(v.z << 16);
-            cc = __uint_as_float(v.x << 16);
-            d = __uint_as_float(v.y << 16);
-        } else {
-            const float4 v = tex2Dgather<float4>(c.tex, g.x, g.y, 0);
-            a = v.w; b = v.z; cc = v.x; d = v.y;
-        }
-    } else {
-        const int i0 = __float_as_int(t.x) - kMagicBits + c.cu;
-        const int j0 = __float_as_int(t.y) - kMagicBits + c.cv;
-        const bool x0 = static_cast<unsigned>(i0) < static_cast<unsigned>(W);
-        const bool x1 = static_cast<unsigned>(i0 + 1) < static_cast<unsigned>(W);
-        const bool y0 = static_cast<unsigned>(j0) < static_cast<unsigned>(H);
-        const bool y1 = static_cast<unsigned>(j0 + 1) < static_cast<unsigned>(H);
-        const ptrdiff_t o = static_cast<ptrdiff_t>(j0) * W + i0;
-        a = (y0 && x0) ? load_px<DT>(c.img, o) : 0.0f;
-        b = (y0 && x1) ? load_px<DT>(c.img, o + 1) : 0.0f;
-        cc = (y1 && x0) ? load_px<DT>(c.img, o + W) : 0.0f;
-        d = (y1 && x1) ? load_px<DT>(c.img, o + W + 1) : 0.0f;
-    }
     const float t0 = fmaf(f.x, b - a, a);
     const float t1 = fmaf(f.x, d - cc, cc);
-    return fmaf(f.y, t1 - t0, t0);
+    acc = fmaf(fmaf(f.y, t1 - t0, t0), w2, acc);
 }
 
-// ROUTE (G_SOFT only): 0 = every z position by texture gather, 1 = every z position by
-// predicated loads, 2 = mixed by the run-time split p.tex_zrun.
-enum Route : int { ROUTE_TEX = 0, ROUTE_LDG = 1, ROUTE_MIX = 2 };
+// Part 2 + 3 by one load of the staged quad element (see ViewParams); same clipping.
+template <int DT>
+__device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 q, float w2, int W, int H,
+                                                float &acc) {
+    const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));
+    const int ix = __float_as_int(t.x) - c.qcx;
+    const int jy = __float_as_int(t.y) - c.qcy;
+    if (static_cast<unsigned>(ix) > static_cast<unsigned>(W) || static_cast<unsigned>(jy) > static_cast<unsigned>(H))
+        return;
+    const size_t e = static_cast<size_t>(jy) * static_cast<unsigned>(W + 1) + static_cast<unsigned>(ix);
+    float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
+    if constexpr (DT == DT_F32) {
+        const float4 v = __ldg(static_cast<const float4 *>(c.quad) + e);
+        ac = make_float2(v.x, v.y);
+        bd = make_float2(v.z, v.w);
+    } else {
+        const uint2 v = __ldg(static_cast<const uint2 *>(c.quad) + e);
+        if constexpr (DT == DT_F16) {
+            ac = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+            bd = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+        } else {
+            ac = make_float2(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u));
+            bd = make_float2(__uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+        }
+    }
+    const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));         // floor(q), exact
+    const float2 f = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), q);          // q - floor(q), exact
+    // both rows lerped along x at once: (t0, t1) = ac + f.x * (bd - ac)
+    const float2 rows = __ffma2_rn(make_float2(f.x, f.x), __ffma2_rn(ac, make_float2(-1.0f, -1.0f), bd), ac);
+    acc = fmaf(fmaf(f.y, rows.y - rows.x, rows.x), w2, acc);
+}
+
+// Part 2 + 3 by four predicated loads from the caller's linear image (no staging); same clipping.
+template <int DT>
+__device__ __forceinline__ void accumulate_ldg(const ViewConsts &c, float2 q, float w2, int W, int H, float &acc) {
+    const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));
+    const int i0 = __float_as_int(t.x) - kMagicBits + c.cu;
+    const int j0 = __float_as_int(t.y) - kMagicBits + c.cv;
+    const bool x0 = static_cast<unsigned>(i0) < static_cast<unsigned>(W);
+    const bool x1 = static_cast<unsigned>(i0 + 1) < static_cast<unsigned>(W);
+    const bool y0 = static_cast<unsigned>(j0) < static_cast<unsigned>(H);
+    const bool y1 = static_cast<unsigned>(j0 + 1) < static_cast<unsigned>(H);
+    if (!((x0 || x1) && (y0 || y1))) return;
+    const ptrdiff_t o = static_cast<ptrdiff_t>(j0) * W + i0;
+    const float a = (y0 && x0) ? load_px<DT>(c.img, o) : 0.0f;
+    const float b = (y0 && x1) ? load_px<DT>(c.img, o + 1) : 0.0f;
+    const float cc = (y1 && x0) ? load_px<DT>(c.img, o + W) : 0.0f;
+    const float d = (y1 && x1) ? load_px<DT>(c.img, o + W + 1) : 0.0f;
+    const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));
+    const float2 f = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), q);
+    const float t0 = fmaf(f.x, b - a, a);
+    const float t1 = fmaf(f.x, d - cc, cc);
+    acc = fmaf(fmaf(f.y, t1 - t0, t0), w2, acc);
+}
 
 template <int G, int DT, int XV, int R, int ROUTE>
 __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParams p) {
@@ -153,9 +211,12 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
         c.w_z = m[10];
         c.cu = v.cu;
         c.cv = v.cv;
-        c.gofs = make_float2(-(kMagic - static_cast<float>(v.cu + 1)), -(kMagic - static_cast<float>(v.cv + 1)));
+        c.gofs = make_float2(v.gofs_x, v.gofs_y);
+        c.qcx = v.qcx;
+        c.qcy = v.qcy;
         c.tex = static_cast<cudaTextureObject_t>(v.tex);
         c.img = v.img;
+        c.quad = v.quad;
         const float2 m_x = make_float2(m[0], m[4]);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -169,20 +230,21 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
                 const float w = (j == 0) ? wr : fmaf(fj, m[8], wr);
                 const float rw = rcp_approx(w);
                 const float2 q = __fmul2_rn(uv, make_float2(rw, rw));
-                float val;
+                const float w2 = rw * rw;
                 if constexpr (G == G_TEXLIN) {
                     // Texture-unit bilinear; the matrix already carries the +0.5 texel-centre shift.
-                    val = tex2D<float>(c.tex, q.x, q.y);
+                    acc[r][j] = fmaf(tex2D<float>(c.tex, q.x, q.y), w2, acc[r][j]);
                 } else if constexpr (ROUTE == ROUTE_TEX) {
-                    val = sample_soft<DT, true>(c, q, p.W, p.H);
+                    accumulate_tex<DT>(c, q, w2, p.W, p.H, acc[r][j]);
                 } else if constexpr (ROUTE == ROUTE_LDG) {
-                    val = sample_soft<DT, false>(c, q, p.W, p.H);
+                    accumulate_ldg<DT>(c, q, w2, p.W, p.H, acc[r][j]);
+                } else if constexpr (ROUTE == ROUTE_QLD) {
+                    accumulate_quad<DT>(c, q, w2, p.W, p.H, acc[r][j]);
                 } else if (r < tex_zrun) {
-                    val = sample_soft<DT, true>(c, q, p.W, p.H);
+                    accumulate_tex<DT>(c, q, w2, p.W, p.H, acc[r][j]);
                 } else {
-                    val = sample_soft<DT, false>(c, q, p.W, p.H);
+                    accumulate_quad<DT>(c, q, w2, p.W, p.H, acc[r][j]);
                 }
-                acc[r][j] = fmaf(val, rw * rw, acc[r][j]);
             }
         }
     }

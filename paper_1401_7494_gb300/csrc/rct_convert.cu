@@ -75,3 +75,51 @@ cudaError_t launch_widen_bf16(const uint16_t *src, float *dst, size_t n, cudaStr
 }
 
 }  // namespace rct
+
+namespace rct {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T px_or_zero(const T *img, int W, int H, int i, int j) {
+    return (static_cast<unsigned>(i) < static_cast<unsigned>(W) && static_cast<unsigned>(j) < static_cast<unsigned>(H))
+               ? img[static_cast<size_t>(j) * W + i] : T(0);
+}
+
+// One thread per padded element (jy, ix): gathers the 2x2 cell with corner (ix - 1, jy - 1).
+__global__ void stage_quads_f32(const float *__restrict__ img, float4 *__restrict__ q, int W, int H) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jy = blockIdx.y;
+    if (ix > W) return;
+    const int i0 = ix - 1, j0 = jy - 1;
+    q[static_cast<size_t>(jy) * (W + 1) + ix] =
+        make_float4(px_or_zero(img, W, H, i0, j0), px_or_zero(img, W, H, i0, j0 + 1),
+                    px_or_zero(img, W, H, i0 + 1, j0), px_or_zero(img, W, H, i0 + 1, j0 + 1));
+}
+
+__global__ void stage_quads_u16(const unsigned short *__restrict__ img, uint2 *__restrict__ q, int W, int H) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jy = blockIdx.y;
+    if (ix > W) return;
+    const int i0 = ix - 1, j0 = jy - 1;
+    const unsigned a = px_or_zero(img, W, H, i0, j0), c = px_or_zero(img, W, H, i0, j0 + 1);
+    const unsigned b = px_or_zero(img, W, H, i0 + 1, j0), d = px_or_zero(img, W, H, i0 + 1, j0 + 1);
+    q[static_cast<size_t>(jy) * (W + 1) + ix] = make_uint2(a | (c << 16), b | (d << 16));
+}
+
+}  // namespace
+
+size_t quad_bytes(int W, int H, int dtype) {
+    return static_cast<size_t>(W + 1) * (H + 1) * (dtype == DT_F32 ? 16 : 8);
+}
+
+cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s) {
+    const dim3 block(256), grid((W + 1 + 255) / 256, H + 1);
+    if (dtype == DT_F32)
+        stage_quads_f32<<<grid, block, 0, s>>>(static_cast<const float *>(src), static_cast<float4 *>(dst), W, H);
+    else
+        stage_quads_u16<<<grid, block, 0, s>>>(static_cast<const unsigned short *>(src), static_cast<uint2 *>(dst), W, H);
+    return cudaGetLastError();
+}
+
+}  // namespace rct

@@ -11,8 +11,10 @@ namespace rct {
 
 constexpr int KMAX = 32;  // views per pass held in the launch parameters
 
-// G_SOFT: software bilinear; per z position of a run the 2x2 cell comes from a texture gather or
-// from predicated global loads (BpParams::tex_zrun).  G_TEXLIN: texture-unit bilinear.
+// G_SOFT: software bilinear; per z position of a run the 2x2 cell comes from a texture gather
+// (z positions [0, tex_zrun)) or from loads (the rest): four predicated loads from the caller's
+// linear image, or, when BpParams::quad is set, one load of a staged quad element holding the
+// whole cell.  G_TEXLIN: texture-unit bilinear.
 enum Gather : int { G_SOFT = 1, G_TEXLIN = 3 };
 enum DType : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 
@@ -24,12 +26,23 @@ enum DType : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 // integer pixel shift (cu, cv) -- the pixel nearest to where the volume
 // centre projects -- keeps u' and v' small, so FP32 rounding of the
 // coordinates stays close to one rounding of the final pixel position.
+//
+// With t = 1.5 * 2^23 + floor(q) (the directed-rounding add in the kernel), the cell's
+// column i0 = cu + floor(q.x); the host precomputes the constants that turn t into the texture
+// gather coordinate (gofs) and into the padded quad index (qcx, qcy).
 struct ViewParams {
     float m[12];               // row-major rows u', v', w
     int cu, cv;                // integer detector shift (0 for texture-filtered sampling)
-    unsigned long long tex;    // cudaTextureObject_t (TLD4, TEXLIN)
-    const void *img;           // linear image, H x W, row-major (LDG)
+    float gofs_x, gofs_y;      // t + gofs = (i0 + 1, j0 + 1): the exact gather corner
+    int qcx, qcy;              // bits(t) - qc = (i0 + 1, j0 + 1): the padded quad index
+    unsigned long long tex;    // cudaTextureObject_t (gather or filtered texture)
+    const void *img;           // linear image, H x W, row-major (plain loads)
+    const void *quad;          // (H + 1) x (W + 1) quad elements, zero padded (quad loads)
 };
+
+// A quad element at padded (row jy, column ix) holds the cell with corner (i0, j0) =
+// (ix - 1, jy - 1) in the order (I[j0][i0], I[j0+1][i0], I[j0][i0+1], I[j0+1][i0+1]), zero where
+// a tap lies off the image; FP32 quads are 16 bytes, FP16/BF16 quads 8 bytes.
 
 struct BpParams {
     float *vol;      // L^3, z-major, x fastest
@@ -38,6 +51,7 @@ struct BpParams {
     float cen;       // (L - 1) / 2
     int accumulate;  // 0: the volume is logically zero, overwrite instead of adding
     int tex_zrun;    // G_SOFT: z positions [0, tex_zrun) of each run use the texture gather
+    int quad;        // G_SOFT: the load route reads staged quad elements (else the linear image)
     ViewParams view[KMAX];
 };
 
@@ -56,6 +70,9 @@ cudaError_t launch_bp_soft_bf16(const LaunchConfig &c, const BpParams &p, cudaSt
 cudaError_t launch_bp_texlin(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
 
 cudaError_t launch_convert(const float *src, void *dst, size_t n, int dtype, cudaStream_t s);
+// Build the zero-padded quad image of one view (see ViewParams) from its linear image.
+cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s);
+size_t quad_bytes(int W, int H, int dtype);
 
 // Record a message for rct_last_error() on the calling thread and return `code`.
 rct_status rct_internal_fail(rct_status code, const char *fmt, ...);
