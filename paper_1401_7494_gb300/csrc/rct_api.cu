@@ -49,6 +49,20 @@ struct Slot {
 
 }  // namespace
 
+void rct::set_view_geometry(ViewParams *vp, const double fold[12], int cu, int cv) {
+    for (int k = 0; k < 4; ++k) {
+        vp->muv[2 * k] = static_cast<float>(fold[k]);          // u' row
+        vp->muv[2 * k + 1] = static_cast<float>(fold[4 + k]);  // v' row
+        vp->mw[k] = static_cast<float>(fold[8 + k]);
+    }
+    vp->cu = cu;
+    vp->cv = cv;
+    vp->gofs_x = -(12582912.0f - static_cast<float>(cu + 1));   // 1.5 * 2^23, the kernel's floor constant
+    vp->gofs_y = -(12582912.0f - static_cast<float>(cv + 1));
+    vp->qcx = 0x4B400000 - cu - 1;
+    vp->qcy = 0x4B400000 - cv - 1;
+}
+
 rct_status rct::rct_internal_fail(rct_status code, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -133,8 +147,7 @@ bool uses_linear(const rct_ctx *c) {
 // Host input must land in linear device memory first when a kernel or a staging step reads it there.
 bool host_needs_linear(const rct_ctx *c) { return uses_linear(c) || uses_quad(c); }
 
-constexpr float kHostMagic = 12582912.0f;   // 1.5 * 2^23, the kernel's floor constant
-constexpr int kHostMagicBits = 0x4B400000;
+
 
 rct_tuning default_tuning(int L) {
     rct_tuning t{};
@@ -215,7 +228,11 @@ rct_status ensure_slots(rct_ctx *c, int n_slots) {
 
 rct_status ensure_copy_machinery(rct_ctx *c) {
     if (c->copy_stream) return RCT_OK;
-    RCT_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    // Highest priority: staging work (copies and quad kernels) must get SMs while a large
+    // backprojection grid is resident, or it would wait for the grid to drain.
+    int least = 0, greatest = 0;
+    RCT_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest), "cudaDeviceGetStreamPriorityRange");
+    RCT_CUDA(cudaStreamCreateWithPriority(&c->copy_stream, cudaStreamNonBlocking, greatest), "cudaStreamCreate");
     for (int i = 0; i < 2; ++i) {
         RCT_CUDA(cudaEventCreateWithFlags(&c->ev_filled[i], cudaEventDisableTiming), "cudaEventCreate");
         RCT_CUDA(cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming), "cudaEventCreate");
@@ -287,13 +304,7 @@ void make_view(const rct_ctx *c, int view, int kind, ViewParams *vp) {
         }
         cu = cv = 0;
     }
-    for (int k = 0; k < 12; ++k) vp->m[k] = static_cast<float>(m[k]);
-    vp->cu = cu;
-    vp->cv = cv;
-    vp->gofs_x = -(kHostMagic - static_cast<float>(cu + 1));
-    vp->gofs_y = -(kHostMagic - static_cast<float>(cv + 1));
-    vp->qcx = kHostMagicBits - cu - 1;
-    vp->qcy = kHostMagicBits - cv - 1;
+    set_view_geometry(vp, m, cu, cv);
     vp->tex = 0;
     vp->img = nullptr;
     vp->quad = nullptr;

@@ -26,7 +26,7 @@
 // The mixed route splits each z-run between the texture gather and the quad
 // load, so both fetch units work side by side (a 2x2 gather of 32-bit texels
 // costs the texture unit two slots).
-// Cells whose four taps are all off the detector are skipped before any fetch.
+// A view is skipped for a warp whose voxel runs all project off the detector.
 // Part 3: three lerps (two of them as one packed f32x2 pair for quads) and
 // acc += val * r^2.
 #pragma once
@@ -80,16 +80,10 @@ struct ViewConsts {
 enum Route : int { ROUTE_TEX = 0, ROUTE_LDG = 1, ROUTE_QLD = 2, ROUTE_MIX = 3 };
 
 // Part 2 + 3 by texture gather: adds the bilinear value at detector (cu + q.x, cv + q.y), times
-// w2, to acc.  A cell whose four taps are all off the detector contributes zero and is skipped
-// before the fetch (the clipping of the paper's Section "Implementation", done per voxel).
+// w2, to acc.  Taps off the detector read the texture's zero border.
 template <int DT>
-__device__ __forceinline__ void accumulate_tex(const ViewConsts &c, float2 q, float w2, int W, int H, float &acc) {
+__device__ __forceinline__ void accumulate_tex(const ViewConsts &c, float2 q, float w2, float &acc) {
     const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));           // kMagic + floor(q)
-    // padded cell index (i0 + 1, j0 + 1): in [0, W] x [0, H] iff some tap is on the image
-    const int ix = __float_as_int(t.x) - c.qcx;
-    const int jy = __float_as_int(t.y) - c.qcy;
-    if (static_cast<unsigned>(ix) > static_cast<unsigned>(W) || static_cast<unsigned>(jy) > static_cast<unsigned>(H))
-        return;
     // The gather footprint of coordinate (i0 + 1, j0 + 1) is exactly texels i0..i0+1 x
     // j0..j0+1 (texel centres at +0.5), independent of the unit's coordinate rounding.
     const float2 g = __fadd2_rn(t, c.gofs);
@@ -111,16 +105,18 @@ __device__ __forceinline__ void accumulate_tex(const ViewConsts &c, float2 q, fl
     acc = fmaf(fmaf(f.y, t1 - t0, t0), w2, acc);
 }
 
-// Part 2 + 3 by one load of the staged quad element (see ViewParams); same clipping.
+// Part 2 + 3 by one load of the staged quad element (see ViewParams).  A cell with no tap on the
+// image has no element; such a lane loads element 0 and adds it with weight 0.
 template <int DT>
 __device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 q, float w2, int W, int H,
                                                 float &acc) {
     const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));
-    const int ix = __float_as_int(t.x) - c.qcx;
+    const int ix = __float_as_int(t.x) - c.qcx;                             // padded index (i0 + 1, j0 + 1)
     const int jy = __float_as_int(t.y) - c.qcy;
-    if (static_cast<unsigned>(ix) > static_cast<unsigned>(W) || static_cast<unsigned>(jy) > static_cast<unsigned>(H))
-        return;
-    const size_t e = static_cast<size_t>(jy) * static_cast<unsigned>(W + 1) + static_cast<unsigned>(ix);
+    const bool on = static_cast<unsigned>(ix) <= static_cast<unsigned>(W) &&
+                    static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
+    const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 1) + static_cast<unsigned>(ix) : 0u;
+    w2 = on ? w2 : 0.0f;
     float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
     if constexpr (DT == DT_F32) {
         const float4 v = __ldg(static_cast<const float4 *>(c.quad) + e);
@@ -143,7 +139,7 @@ __device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 q, f
     acc = fmaf(fmaf(f.y, rows.y - rows.x, rows.x), w2, acc);
 }
 
-// Part 2 + 3 by four predicated loads from the caller's linear image (no staging); same clipping.
+// Part 2 + 3 by four predicated loads from the caller's linear image (no staging).
 template <int DT>
 __device__ __forceinline__ void accumulate_ldg(const ViewConsts &c, float2 q, float w2, int W, int H, float &acc) {
     const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));
@@ -153,7 +149,6 @@ __device__ __forceinline__ void accumulate_ldg(const ViewConsts &c, float2 q, fl
     const bool x1 = static_cast<unsigned>(i0 + 1) < static_cast<unsigned>(W);
     const bool y0 = static_cast<unsigned>(j0) < static_cast<unsigned>(H);
     const bool y1 = static_cast<unsigned>(j0 + 1) < static_cast<unsigned>(H);
-    if (!((x0 || x1) && (y0 || y1))) return;
     const ptrdiff_t o = static_cast<ptrdiff_t>(j0) * W + i0;
     const float a = (y0 && x0) ? load_px<DT>(c.img, o) : 0.0f;
     const float b = (y0 && x1) ? load_px<DT>(c.img, o + 1) : 0.0f;
@@ -164,6 +159,14 @@ __device__ __forceinline__ void accumulate_ldg(const ViewConsts &c, float2 q, fl
     const float t0 = fmaf(f.x, b - a, a);
     const float t1 = fmaf(f.x, d - cc, cc);
     acc = fmaf(fmaf(f.y, t1 - t0, t0), w2, acc);
+}
+
+// Padded cell index (i0 + 1, j0 + 1) of the voxel at (u', v', w); a cell with a tap on the
+// image has it in [0, W] x [0, H].
+__device__ __forceinline__ int2 cell_index(const ViewConsts &c, float2 uv, float w) {
+    const float rw = rcp_approx(w);
+    const float2 t = __fadd2_rd(__fmul2_rn(uv, make_float2(rw, rw)), make_float2(kMagic, kMagic));
+    return make_int2(__float_as_int(t.x) - c.qcx, __float_as_int(t.y) - c.qcy);
 }
 
 template <int G, int DT, int XV, int R, int ROUTE>
@@ -201,14 +204,16 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
 #pragma unroll 1
     for (int k = 0; k < p.K; ++k) {
         const ViewParams &v = p.view[k];
-        const float *m = v.m;
+        const float2 *muv = reinterpret_cast<const float2 *>(v.muv);
+        const float *mw = v.mw;
         // Part 1 at the thread's first voxel; (u', v') travel as one f32x2 pair.
-        const float2 buv = make_float2(fmaf(m[0], xc0, fmaf(m[1], yc, fmaf(m[2], zc0, m[3]))),
-                                       fmaf(m[4], xc0, fmaf(m[5], yc, fmaf(m[6], zc0, m[7]))));
-        const float bw = fmaf(m[8], xc0, fmaf(m[9], yc, fmaf(m[10], zc0, m[11])));
+        const float2 buv = __ffma2_rn(make_float2(xc0, xc0), muv[0],
+                                      __ffma2_rn(make_float2(yc, yc), muv[1],
+                                                 __ffma2_rn(make_float2(zc0, zc0), muv[2], muv[3])));
+        const float bw = fmaf(mw[0], xc0, fmaf(mw[1], yc, fmaf(mw[2], zc0, mw[3])));
         ViewConsts c;
-        c.m_z = make_float2(m[2], m[6]);
-        c.w_z = m[10];
+        c.m_z = muv[2];
+        c.w_z = mw[2];
         c.cu = v.cu;
         c.cv = v.cv;
         c.gofs = make_float2(v.gofs_x, v.gofs_y);
@@ -217,7 +222,31 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
         c.tex = static_cast<cudaTextureObject_t>(v.tex);
         c.img = v.img;
         c.quad = v.quad;
-        const float2 m_x = make_float2(m[0], m[4]);
+        const float2 m_x = muv[0];
+        if constexpr (G == G_SOFT) {
+            // Clipping per run (the paper's clipping mask, Section "Implementation"): the
+            // thread's voxels form a segment (XV = 1) or parallelogram in (x, z); its projection
+            // is the convex hull of the corners' projections.  If every corner's cell lies on the
+            // same outer side of the detector, no voxel of the run touches the image.  When that
+            // holds for the whole warp, the view is skipped.
+            bool left = true, right = true, top = true, bottom = true;
+#pragma unroll
+            for (int cr = 0; cr < (R > 1 ? 2 : 1); ++cr) {
+#pragma unroll
+                for (int cj = 0; cj < (XV > 1 ? 2 : 1); ++cj) {
+                    const float fr = cr ? static_cast<float>(R - 1) : 0.0f;
+                    const float fj = cj ? static_cast<float>(XV - 1) : 0.0f;
+                    const float2 uv = __ffma2_rn(make_float2(fj, fj), m_x, __ffma2_rn(make_float2(fr, fr), c.m_z, buv));
+                    const float w = fmaf(fj, mw[0], fmaf(fr, c.w_z, bw));
+                    const int2 ci = cell_index(c, uv, w);
+                    left = left && ci.x < 0;
+                    right = right && ci.x > p.W;
+                    top = top && ci.y < 0;
+                    bottom = bottom && ci.y > p.H;
+                }
+            }
+            if (__all_sync(0xffffffffu, left || right || top || bottom)) continue;
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float fr = static_cast<float>(r);
@@ -227,7 +256,7 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
             for (int j = 0; j < XV; ++j) {
                 const float fj = static_cast<float>(j);
                 const float2 uv = (j == 0) ? uvr : __ffma2_rn(make_float2(fj, fj), m_x, uvr);
-                const float w = (j == 0) ? wr : fmaf(fj, m[8], wr);
+                const float w = (j == 0) ? wr : fmaf(fj, mw[0], wr);
                 const float rw = rcp_approx(w);
                 const float2 q = __fmul2_rn(uv, make_float2(rw, rw));
                 const float w2 = rw * rw;
@@ -235,13 +264,13 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
                     // Texture-unit bilinear; the matrix already carries the +0.5 texel-centre shift.
                     acc[r][j] = fmaf(tex2D<float>(c.tex, q.x, q.y), w2, acc[r][j]);
                 } else if constexpr (ROUTE == ROUTE_TEX) {
-                    accumulate_tex<DT>(c, q, w2, p.W, p.H, acc[r][j]);
+                    accumulate_tex<DT>(c, q, w2, acc[r][j]);
                 } else if constexpr (ROUTE == ROUTE_LDG) {
                     accumulate_ldg<DT>(c, q, w2, p.W, p.H, acc[r][j]);
                 } else if constexpr (ROUTE == ROUTE_QLD) {
                     accumulate_quad<DT>(c, q, w2, p.W, p.H, acc[r][j]);
                 } else if (r < tex_zrun) {
-                    accumulate_tex<DT>(c, q, w2, p.W, p.H, acc[r][j]);
+                    accumulate_tex<DT>(c, q, w2, acc[r][j]);
                 } else {
                     accumulate_quad<DT>(c, q, w2, p.W, p.H, acc[r][j]);
                 }

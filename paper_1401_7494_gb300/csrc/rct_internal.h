@@ -31,7 +31,8 @@ enum DType : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 // column i0 = cu + floor(q.x); the host precomputes the constants that turn t into the texture
 // gather coordinate (gofs) and into the padded quad index (qcx, qcy).
 struct ViewParams {
-    float m[12];               // row-major rows u', v', w
+    float muv[8];              // rows u', v' interleaved: (m0, m4), (m1, m5), (m2, m6), (m3, m7)
+    float mw[4];               // row w
     int cu, cv;                // integer detector shift (0 for texture-filtered sampling)
     float gofs_x, gofs_y;      // t + gofs = (i0 + 1, j0 + 1): the exact gather corner
     int qcx, qcy;              // bits(t) - qc = (i0 + 1, j0 + 1): the padded quad index
@@ -73,6 +74,10 @@ cudaError_t launch_convert(const float *src, void *dst, size_t n, int dtype, cud
 // Build the zero-padded quad image of one view (see ViewParams) from its linear image.
 cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s);
 size_t quad_bytes(int W, int H, int dtype);
+
+// Fill the matrix and the index constants of a view from its FP64 fold (rows u', v', w over
+// centred voxel coordinates) and integer detector shift.
+void set_view_geometry(ViewParams *vp, const double fold[12], int cu, int cv);
 
 // Record a message for rct_last_error() on the calling thread and return `code`.
 rct_status rct_internal_fail(rct_status code, const char *fmt, ...);

@@ -124,9 +124,7 @@ extern "C" rct_status rct_backproject_f16_noalloc(int L, int det_w, int det_h, c
                                               fold, shift);
             if (st != RCT_OK) return st;
             ViewParams &vp = p.view[k];
-            for (int i = 0; i < 12; ++i) vp.m[i] = static_cast<float>(fold[i]);
-            vp.cu = shift[0];
-            vp.cv = shift[1];
+            set_view_geometry(&vp, fold, shift[0], shift[1]);
             vp.tex = 0;
             vp.img = scratch + static_cast<size_t>(k) * px;
         }
