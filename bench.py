@@ -283,11 +283,12 @@ def run_ours(args, dist: Dist) -> dict | None:
     passes_per_step = -(-w.n_views // K)
     upd_per_launch = w.updates / passes_per_step
     kernel_gups = upd_per_launch / avg_kernel_s / 1e9
-    px_per_voxel = (w.geom.sdd / w.geom.sid) * float(w.spacing[0]) / w.geom.pitch
-    tex_peak = rct.rct_probe_texture(0, rct.RCT_PROJ_F32, px_per_voxel, px_per_voxel, 4096) / 1e9
-    ldg_peak = rct.rct_probe_texture(3, rct.RCT_PROJ_F32, px_per_voxel, px_per_voxel, 4096) / 1e9
-    route = {rct.RCT_GATHER_LDG: "ldg", rct.RCT_GATHER_MIX: "mix"}.get(tun.get("gather"), "tex")
-    fetch_peak = {"tex": tex_peak, "ldg": ldg_peak, "mix": tex_peak + ldg_peak}[route]
+    px_per_voxel = min(8.0, (w.geom.sdd / w.geom.sid) * float(w.spacing[0]) / w.geom.pitch)
+    route = {rct.RCT_GATHER_LDG: "ldg", rct.RCT_GATHER_MIX: "mix", rct.RCT_GATHER_QUAD: "qld",
+             rct.RCT_GATHER_PAIR: "pld"}.get(tun.get("gather"), "tex")
+    probe = lambda mode: rct.rct_probe_texture(mode, rct.RCT_PROJ_F32, px_per_voxel, px_per_voxel, 4096) / 1e9
+    ceilings = {"tex": probe(0), "ldg": probe(3), "qld": probe(4), "pld": probe(5)}
+    fetch_peak = ceilings["tex"] + ceilings["qld"] if route == "mix" else ceilings[route]
     vol_bytes = 4 * w.L ** 3
     img_bytes = 4 * w.geom.det_w * w.geom.det_h
     # per step: the first pass writes only, later passes read and write; each view's image is read once
@@ -299,8 +300,9 @@ def run_ours(args, dist: Dist) -> dict | None:
                 "unit": "G cell-fetches/s (one 2x2 fetch per voxel update)",
                 "frac": round(kernel_gups / fetch_peak, 4), "traffic": None,
                 "kernel": f"bp_kernel, {route} route", "route": route,
-                "peak_source": f"measured live: tld4 FP32 gather probe {tex_peak:.1f} G/s + 4-load gather probe "
-                               f"{ldg_peak:.1f} G/s at lane stride {px_per_voxel:.2f} px",
+                "peak_source": ("measured live with the library's fetch probes at this workload's lane stride "
+                                f"({px_per_voxel:.2f} px): " + ", ".join(f"{k} {v:.1f} G/s" for k, v in ceilings.items())
+                                + ("; mixed route: tex + qld" if route == "mix" else "")),
                 "kernel_share_of_step": round(kernel_ms / ms_total, 4), "updates_per_launch": int(upd_per_launch),
                 "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                         "frac": round(achieved_gbs / hbm_peak, 4), "algorithmic_bytes_per_launch": int(bytes_per_launch),

@@ -83,8 +83,10 @@ typedef enum rct_gather {
     RCT_GATHER_TLD4 = 2,  /* one texture gather (tld4) of the 2x2 cell from a staged copy */
     RCT_GATHER_MIX = 3,   /* per z-run: the first tex_zrun positions by tld4, the rest by quad loads
                              (below), so the texture and load/store pipes work side by side */
-    RCT_GATHER_QUAD = 4   /* one 128-bit load (64-bit for 16-bit data) of a staged, zero-padded "quad"
+    RCT_GATHER_QUAD = 4,  /* one 128-bit load (64-bit for 16-bit data) of a staged, zero-padded "quad"
                              copy of the image whose every element holds a whole 2x2 cell */
+    RCT_GATHER_PAIR = 5   /* two 64-bit loads (32-bit for 16-bit data) of a staged, zero-padded copy
+                             whose every element holds two vertically adjacent pixels */
 } rct_gather;
 
 /* Kernel tuning.  Zero in any field means "keep the current value". */
@@ -243,10 +245,13 @@ RCT_API rct_status rct_fold_geometry(int L, int n_views, const double *matrices,
  * Throughput probes (measurement support, allocate their own small buffers).
  * rct_probe_texture: fetches per second over the whole GPU for texture fetches
  * of one kind -- mode 0 = tld4 gather, 1 = point fetch, 2 = bilinear filtered
- * fetch, 3 = four predicated global loads of the 2x2 cell (FP32 only) --
+ * fetch, 3 = four predicated global loads of the 2x2 cell (FP32 only), 4 = one
+ * 16-byte quad load, 5 = two 8-byte pair loads (4 and 5: FP32 staged layouts over
+ * a 1280 x 1024-element buffer that lives in L2, not L1) --
  * from a 256x256 texture (or linear image) of dtype RCT_PROJ_F32 or RCT_PROJ_F16 that
  * stays cache resident; neighbouring lanes sample stride_px apart along x and
- * each fetch advances step_px along y.  rct_probe_update_stream: bytes read +
+ * each fetch advances step_px along y (stride 0..10 px, step 0..8 px, else
+ * RCT_EINVAL).  rct_probe_update_stream: bytes read +
  * written per second by a float4 read-modify-write sweep over `bytes` of
  * device memory (the paper's "Node Update" benchmark, Table 1).
  */

@@ -20,9 +20,9 @@ from . import rct, tuning
 
 CANDIDATES = {
     # (gather route, z positions per run through the texture gather when mixed)
-    "gather": [(rct.RCT_GATHER_TLD4, 0), (rct.RCT_GATHER_LDG, 0), (rct.RCT_GATHER_QUAD, 0), (rct.RCT_GATHER_MIX, 1),
-               (rct.RCT_GATHER_MIX, 2), (rct.RCT_GATHER_MIX, 3), (rct.RCT_GATHER_MIX, 4),
-               (rct.RCT_GATHER_MIX, 5), (rct.RCT_GATHER_MIX, 6)],
+    "gather": [(rct.RCT_GATHER_TLD4, 0), (rct.RCT_GATHER_LDG, 0), (rct.RCT_GATHER_QUAD, 0),
+               (rct.RCT_GATHER_PAIR, 0), (rct.RCT_GATHER_MIX, 1), (rct.RCT_GATHER_MIX, 2),
+               (rct.RCT_GATHER_MIX, 4), (rct.RCT_GATHER_MIX, 6)],
     "views_per_pass": [4, 8, 16, 24, 32],
     "zrun": [1, 2, 4, 8],
     "xvec": [1, 2, 4],

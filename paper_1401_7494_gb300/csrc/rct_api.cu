@@ -124,7 +124,8 @@ int tex_zrun_of(const rct_ctx *c) {
     const int R = c->tune.zrun;
     switch (c->tune.gather) {
         case RCT_GATHER_LDG:
-        case RCT_GATHER_QUAD: return 0;
+        case RCT_GATHER_QUAD:
+        case RCT_GATHER_PAIR: return 0;
         case RCT_GATHER_MIX: return R <= 1 ? R : std::min(std::max(c->tune.tex_zrun, 1), R - 1);
         default: return R;
     }
@@ -132,9 +133,22 @@ int tex_zrun_of(const rct_ctx *c) {
 
 bool uses_tex(const rct_ctx *c) { return kernel_kind(c) == G_TEXLIN || tex_zrun_of(c) > 0; }
 
-// The load part of the software route reads staged quad elements (QUAD, MIX).
-bool uses_quad(const rct_ctx *c) {
-    return kernel_kind(c) == G_SOFT && c->tune.gather != RCT_GATHER_LDG && tex_zrun_of(c) < c->tune.zrun;
+// Staged layout the load part of the software route reads: 0 = none (texture only, or the
+// caller's linear image), 1 = quads (QUAD, MIX), 2 = vertical pairs (PAIR).
+int load_layout(const rct_ctx *c) {
+    if (kernel_kind(c) != G_SOFT || c->tune.gather == RCT_GATHER_LDG || tex_zrun_of(c) >= c->tune.zrun) return 0;
+    return c->tune.gather == RCT_GATHER_PAIR ? 2 : 1;
+}
+
+bool uses_quad(const rct_ctx *c) { return load_layout(c) != 0; }
+
+size_t layout_bytes(const rct_ctx *c) {
+    return load_layout(c) == 2 ? pair_bytes(c->W, c->H, c->dtype) : quad_bytes(c->W, c->H, c->dtype);
+}
+
+cudaError_t launch_stage_layout(const rct_ctx *c, const void *src, void *dst, cudaStream_t s) {
+    return load_layout(c) == 2 ? launch_stage_pairs(src, dst, c->W, c->H, c->dtype, s)
+                               : launch_stage_quads(src, dst, c->W, c->H, c->dtype, s);
 }
 
 // The kernel reads the caller's linear image (LDG route), or BF16 must be widened before a
@@ -242,7 +256,7 @@ rct_status ensure_copy_machinery(rct_ctx *c) {
 
 rct_status ensure_quads(rct_ctx *c, int n_slots) {
     if (!uses_quad(c)) return RCT_OK;
-    const size_t need = (size_t)n_slots * quad_bytes(c->W, c->H, c->dtype);
+    const size_t need = (size_t)n_slots * layout_bytes(c);
     if (c->quad_alloc >= need) return RCT_OK;
     if (c->quad_buf) cudaFree(c->quad_buf);
     c->quad_buf = nullptr;
@@ -254,7 +268,7 @@ rct_status ensure_quads(rct_ctx *c, int n_slots) {
 }
 
 void *quad_slot(const rct_ctx *c, int slot) {
-    return static_cast<char *>(c->quad_buf) + (size_t)slot * quad_bytes(c->W, c->H, c->dtype);
+    return static_cast<char *>(c->quad_buf) + (size_t)slot * layout_bytes(c);
 }
 
 rct_status ensure_widen(rct_ctx *c, size_t elems) {
@@ -287,7 +301,7 @@ void init_params(const rct_ctx *c, BpParams *p) {
     p->H = c->H;
     p->cen = 0.5f * (c->L - 1);
     p->tex_zrun = tex_zrun_of(c);
-    p->quad = uses_quad(c) ? 1 : 0;
+    p->quad = load_layout(c);
 }
 
 // FP32 view parameters for one view and kernel kind, from the FP64 fold.
@@ -542,7 +556,7 @@ rct_status rct_set_tuning(rct_ctx *c, const rct_tuning *t) {
     if (c->L % n.xvec != 0) return fail(RCT_EINVAL, "xvec %d does not divide L = %d", n.xvec, c->L);
     if (n.block_x < 1 || n.block_y < 1 || n.block_x * n.block_y > 512 || (n.block_x * n.block_y) % 32 != 0)
         return fail(RCT_EINVAL, "block %dx%d: need a multiple of 32 threads, at most 512", n.block_x, n.block_y);
-    if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_QUAD) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
+    if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_PAIR) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
     if (n.tex_zrun < 0 || n.tex_zrun > 8) return fail(RCT_EINVAL, "tex_zrun %d outside 0..8", n.tex_zrun);
     c->tune = n;
     return RCT_OK;
@@ -618,8 +632,8 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
             }
             if (quad) {
                 vp.quad = quad_slot(c, g * K + k);
-                cudaError_t e = launch_stage_quads(src, const_cast<void *>(vp.quad), c->W, c->H, c->dtype, c->copy_stream);
-                if (e != cudaSuccess) return cuda_fail(e, "quad staging kernel");
+                cudaError_t e = launch_stage_layout(c, src, const_cast<void *>(vp.quad), c->copy_stream);
+                if (e != cudaSuccess) return cuda_fail(e, "quad/pair staging kernel");
             }
         }
         if (staged) {
@@ -676,8 +690,8 @@ rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, 
                 if (slot && (st = stage_view(c, *slot, lin, false, c->copy_stream))) return st;
                 if (quad) {
                     vp.quad = quad_slot(c, g * K + k);
-                    cudaError_t e = launch_stage_quads(lin, const_cast<void *>(vp.quad), c->W, c->H, c->dtype, c->copy_stream);
-                    if (e != cudaSuccess) return cuda_fail(e, "quad staging kernel");
+                    cudaError_t e = launch_stage_layout(c, lin, const_cast<void *>(vp.quad), c->copy_stream);
+                    if (e != cudaSuccess) return cuda_fail(e, "quad/pair staging kernel");
                 }
                 vp.img = lin;
             } else if (slot) {

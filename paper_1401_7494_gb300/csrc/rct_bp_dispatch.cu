@@ -9,6 +9,7 @@ namespace rct {
     cudaError_t launch_bp_soft_##dt##_tex(const LaunchConfig &, const BpParams &, cudaStream_t); \
     cudaError_t launch_bp_soft_##dt##_ldg(const LaunchConfig &, const BpParams &, cudaStream_t); \
     cudaError_t launch_bp_soft_##dt##_qld(const LaunchConfig &, const BpParams &, cudaStream_t); \
+    cudaError_t launch_bp_soft_##dt##_pld(const LaunchConfig &, const BpParams &, cudaStream_t); \
     cudaError_t launch_bp_soft_##dt##_mix(const LaunchConfig &, const BpParams &, cudaStream_t);
 RCT_DECLARE_ROUTES(f32)
 RCT_DECLARE_ROUTES(f16)
@@ -16,7 +17,10 @@ RCT_DECLARE_ROUTES(bf16)
 #undef RCT_DECLARE_ROUTES
 
 #define RCT_ROUTE_SWITCH(dt)                                                                      \
-    if (p.tex_zrun <= 0) return p.quad ? launch_bp_soft_##dt##_qld(c, p, s) : launch_bp_soft_##dt##_ldg(c, p, s); \
+    if (p.tex_zrun <= 0) {                                                                        \
+        if (p.quad == 2) return launch_bp_soft_##dt##_pld(c, p, s);                               \
+        return p.quad ? launch_bp_soft_##dt##_qld(c, p, s) : launch_bp_soft_##dt##_ldg(c, p, s);  \
+    }                                                                                             \
     if (p.tex_zrun < c.zrun) return launch_bp_soft_##dt##_mix(c, p, s);                           \
     return launch_bp_soft_##dt##_tex(c, p, s);
 

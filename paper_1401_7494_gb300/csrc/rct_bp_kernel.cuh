@@ -77,7 +77,8 @@ struct ViewConsts {
 //   ROUTE_TEX: every z position by texture gather;  ROUTE_LDG: every z position by four
 //   predicated loads from the linear image;  ROUTE_QLD: every z position by one quad load;
 //   ROUTE_MIX: z positions [0, tex_zrun) by texture gather, the rest by quad loads.
-enum Route : int { ROUTE_TEX = 0, ROUTE_LDG = 1, ROUTE_QLD = 2, ROUTE_MIX = 3 };
+//   ROUTE_PLD: every z position by two loads of staged vertical pairs.
+enum Route : int { ROUTE_TEX = 0, ROUTE_LDG = 1, ROUTE_QLD = 2, ROUTE_MIX = 3, ROUTE_PLD = 4 };
 
 // Part 2 + 3 by texture gather: adds the bilinear value at detector (cu + q.x, cv + q.y), times
 // w2, to acc.  Taps off the detector read the texture's zero border.
@@ -135,6 +136,40 @@ __device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 q, f
     const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));         // floor(q), exact
     const float2 f = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), q);          // q - floor(q), exact
     // both rows lerped along x at once: (t0, t1) = ac + f.x * (bd - ac)
+    const float2 rows = __ffma2_rn(make_float2(f.x, f.x), __ffma2_rn(ac, make_float2(-1.0f, -1.0f), bd), ac);
+    acc = fmaf(fmaf(f.y, rows.y - rows.x, rows.x), w2, acc);
+}
+
+// Part 2 + 3 by two loads of consecutive staged vertical pairs (see ViewParams): neighbouring
+// lanes share cache sectors, so less data moves from L2 than with quads.  Same off-image rule.
+template <int DT>
+__device__ __forceinline__ void accumulate_pair(const ViewConsts &c, float2 q, float w2, int W, int H,
+                                                float &acc) {
+    const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));
+    const int ix = __float_as_int(t.x) - c.qcx;                             // padded index (i0 + 1, j0 + 1)
+    const int jy = __float_as_int(t.y) - c.qcy;
+    const bool on = static_cast<unsigned>(ix) <= static_cast<unsigned>(W) &&
+                    static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
+    const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 2) + static_cast<unsigned>(ix) : 0u;
+    w2 = on ? w2 : 0.0f;
+    float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
+    if constexpr (DT == DT_F32) {
+        const float2 *pp = static_cast<const float2 *>(c.quad) + e;
+        ac = __ldg(pp);
+        bd = __ldg(pp + 1);
+    } else {
+        const unsigned *pp = static_cast<const unsigned *>(c.quad) + e;
+        const unsigned v0 = __ldg(pp), v1 = __ldg(pp + 1);
+        if constexpr (DT == DT_F16) {
+            ac = __half22float2(*reinterpret_cast<const __half2 *>(&v0));
+            bd = __half22float2(*reinterpret_cast<const __half2 *>(&v1));
+        } else {
+            ac = make_float2(__uint_as_float(v0 << 16), __uint_as_float(v0 & 0xffff0000u));
+            bd = make_float2(__uint_as_float(v1 << 16), __uint_as_float(v1 & 0xffff0000u));
+        }
+    }
+    const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));
+    const float2 f = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), q);
     const float2 rows = __ffma2_rn(make_float2(f.x, f.x), __ffma2_rn(ac, make_float2(-1.0f, -1.0f), bd), ac);
     acc = fmaf(fmaf(f.y, rows.y - rows.x, rows.x), w2, acc);
 }
@@ -269,6 +304,8 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
                     accumulate_ldg<DT>(c, q, w2, p.W, p.H, acc[r][j]);
                 } else if constexpr (ROUTE == ROUTE_QLD) {
                     accumulate_quad<DT>(c, q, w2, p.W, p.H, acc[r][j]);
+                } else if constexpr (ROUTE == ROUTE_PLD) {
+                    accumulate_pair<DT>(c, q, w2, p.W, p.H, acc[r][j]);
                 } else if (r < tex_zrun) {
                     accumulate_tex<DT>(c, q, w2, acc[r][j]);
                 } else {

@@ -107,7 +107,37 @@ __global__ void stage_quads_u16(const unsigned short *__restrict__ img, uint2 *_
     q[static_cast<size_t>(jy) * (W + 1) + ix] = make_uint2(a | (c << 16), b | (d << 16));
 }
 
+// One thread per padded pair (jy, ix): (I[jy-1][ix-1], I[jy][ix-1]), zero off the image.
+__global__ void stage_pairs_f32(const float *__restrict__ img, float2 *__restrict__ q, int W, int H) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jy = blockIdx.y;
+    if (ix > W + 1) return;
+    q[static_cast<size_t>(jy) * (W + 2) + ix] =
+        make_float2(px_or_zero(img, W, H, ix - 1, jy - 1), px_or_zero(img, W, H, ix - 1, jy));
+}
+
+__global__ void stage_pairs_u16(const unsigned short *__restrict__ img, unsigned *__restrict__ q, int W, int H) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jy = blockIdx.y;
+    if (ix > W + 1) return;
+    const unsigned a = px_or_zero(img, W, H, ix - 1, jy - 1), c = px_or_zero(img, W, H, ix - 1, jy);
+    q[static_cast<size_t>(jy) * (W + 2) + ix] = a | (c << 16);
+}
+
 }  // namespace
+
+size_t pair_bytes(int W, int H, int dtype) {
+    return static_cast<size_t>(W + 2) * (H + 1) * (dtype == DT_F32 ? 8 : 4);
+}
+
+cudaError_t launch_stage_pairs(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s) {
+    const dim3 block(256), grid((W + 2 + 255) / 256, H + 1);
+    if (dtype == DT_F32)
+        stage_pairs_f32<<<grid, block, 0, s>>>(static_cast<const float *>(src), static_cast<float2 *>(dst), W, H);
+    else
+        stage_pairs_u16<<<grid, block, 0, s>>>(static_cast<const unsigned short *>(src), static_cast<unsigned *>(dst), W, H);
+    return cudaGetLastError();
+}
 
 size_t quad_bytes(int W, int H, int dtype) {
     return static_cast<size_t>(W + 1) * (H + 1) * (dtype == DT_F32 ? 16 : 8);

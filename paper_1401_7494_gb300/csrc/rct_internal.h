@@ -38,12 +38,16 @@ struct ViewParams {
     int qcx, qcy;              // bits(t) - qc = (i0 + 1, j0 + 1): the padded quad index
     unsigned long long tex;    // cudaTextureObject_t (gather or filtered texture)
     const void *img;           // linear image, H x W, row-major (plain loads)
-    const void *quad;          // (H + 1) x (W + 1) quad elements, zero padded (quad loads)
+    const void *quad;          // staged quad or pair image, zero padded (quad / pair loads)
 };
 
 // A quad element at padded (row jy, column ix) holds the cell with corner (i0, j0) =
 // (ix - 1, jy - 1) in the order (I[j0][i0], I[j0+1][i0], I[j0][i0+1], I[j0+1][i0+1]), zero where
 // a tap lies off the image; FP32 quads are 16 bytes, FP16/BF16 quads 8 bytes.
+// A pair element at padded (row jy, column ix) holds the vertical pair (I[jy-1][ix-1], I[jy][ix-1]);
+// the image has H + 1 rows of W + 2 pairs, and the cell with corner (i0, j0) is the two
+// consecutive pairs at (j0 + 1, i0 + 1) and (j0 + 1, i0 + 2).  FP32 pairs are 8 bytes, FP16/BF16
+// pairs 4 bytes.
 
 struct BpParams {
     float *vol;      // L^3, z-major, x fastest
@@ -52,7 +56,7 @@ struct BpParams {
     float cen;       // (L - 1) / 2
     int accumulate;  // 0: the volume is logically zero, overwrite instead of adding
     int tex_zrun;    // G_SOFT: z positions [0, tex_zrun) of each run use the texture gather
-    int quad;        // G_SOFT: the load route reads staged quad elements (else the linear image)
+    int quad;        // G_SOFT load route: 0 = linear image, 1 = staged quads, 2 = staged pairs
     ViewParams view[KMAX];
 };
 
@@ -74,6 +78,9 @@ cudaError_t launch_convert(const float *src, void *dst, size_t n, int dtype, cud
 // Build the zero-padded quad image of one view (see ViewParams) from its linear image.
 cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s);
 size_t quad_bytes(int W, int H, int dtype);
+// Build the zero-padded vertical-pair image of one view (see ViewParams).
+cudaError_t launch_stage_pairs(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s);
+size_t pair_bytes(int W, int H, int dtype);
 
 // Fill the matrix and the index constants of a view from its FP64 fold (rows u', v', w over
 // centred voxel coordinates) and integer detector shift.

@@ -67,6 +67,36 @@ __global__ void __launch_bounds__(256) ldg4_probe_kernel(const float *__restrict
     if (acc == 1.2345e-30f) sink[0] = acc;
 }
 
+// Staged-layout loads over a detector-sized buffer (larger than L1, resident in L2): one 16-byte
+// quad (PAIRS = false) or two consecutive 8-byte pairs (PAIRS = true) per fetch, same lane layout.
+constexpr int kLayoutW = 1280, kLayoutH = 1024;
+
+template <bool PAIRS>
+__global__ void __launch_bounds__(256) layout_probe_kernel(const float4 *__restrict__ quads, int iters, float stride,
+                                                           float step, float *sink) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    float x = 8.0f + lane * stride + (warp % 11) * 100.0f;
+    float y = 8.0f + ((warp / 11) % 97) * 9.0f;
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+        const int ix = __float2int_rd(x), jy = __float2int_rd(y);
+        const unsigned e = static_cast<unsigned>(jy) * kLayoutW + static_cast<unsigned>(ix);
+        if constexpr (PAIRS) {
+            const float2 *pp = reinterpret_cast<const float2 *>(quads) + e;
+            const float2 a = __ldg(pp), b = __ldg(pp + 1);
+            acc += (a.x + a.y) + (b.x + b.y);
+        } else {
+            const float4 v = __ldg(quads + e);
+            acc += (v.x + v.y) + (v.z + v.w);
+        }
+        y += step;
+        y = (y > kLayoutH - 16.0f) ? y - (kLayoutH - 32.0f) : y;
+    }
+    if (acc == 1.2345e-30f) sink[0] = acc;
+}
+
 __global__ void update_stream_kernel(float4 *__restrict__ a, size_t n4, float s) {
     const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
     for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
@@ -81,14 +111,16 @@ __global__ void update_stream_kernel(float4 *__restrict__ a, size_t n4, float s)
 extern "C" {
 
 // mode: 0 = tld4 gather (point texture), 1 = point fetch, 2 = bilinear filtered fetch,
-// 3 = four predicated global loads of the 2x2 cell (FP32 only; the load/store route).
+// 3 = four predicated global loads of the 2x2 cell (FP32 only; the load/store route),
+// 4 = one 16-byte quad load, 5 = two 8-byte pair loads (FP32 layouts over a 1280 x 1024 buffer).
 // dtype: RCT_PROJ_F32 or RCT_PROJ_F16 texels.  stride_px: x distance between neighbouring lanes,
 // step_px: y advance per fetch.  Writes fetches per second (whole GPU) to *rate.
 RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float step_px, int iters,
                                      double *rate) {
-    if (!rate || mode < 0 || mode > 3 || iters <= 0 || (dtype != RCT_PROJ_F32 && dtype != RCT_PROJ_F16))
+    if (!rate || mode < 0 || mode > 5 || iters <= 0 || (dtype != RCT_PROJ_F32 && dtype != RCT_PROJ_F16))
         return RCT_EINVAL;
-    if (mode == 3 && dtype != RCT_PROJ_F32) return RCT_EINVAL;
+    if (mode >= 3 && dtype != RCT_PROJ_F32) return RCT_EINVAL;
+    if (stride_px < 0.0f || stride_px > 10.0f || step_px < 0.0f || step_px > 8.0f) return RCT_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RCT_ECUDA;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -101,8 +133,10 @@ RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float
     rct_status st = RCT_ECUDA;
     do {
         if (cudaMallocArray(&arr, &fmt, kTexSide, kTexSide, mode == 0 ? cudaArrayTextureGather : 0) != cudaSuccess) break;
-        if (cudaMalloc(&sink, sizeof(float) * (1 + kTexSide * kTexSide)) != cudaSuccess) break;
-        if (cudaMemset(sink, 0, sizeof(float) * (1 + kTexSide * kTexSide)) != cudaSuccess) break;
+        // sink[0]: result sink; then a 256 x 256 float image (mode 3) or a 1280 x 1024 float4 layout buffer
+        const size_t floats = 4 + static_cast<size_t>(kLayoutW) * kLayoutH * 4;
+        if (cudaMalloc(&sink, sizeof(float) * floats) != cudaSuccess) break;
+        if (cudaMemset(sink, 0, sizeof(float) * floats) != cudaSuccess) break;
         cudaResourceDesc rd{};
         rd.resType = cudaResourceTypeArray;
         rd.res.array.array = arr;
@@ -114,7 +148,11 @@ RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) break;
         const int block = 256, grid = sms * 8;
         auto run = [&]() {
-            if (mode == 3) ldg4_probe_kernel<<<grid, block>>>(sink + 1, iters, stride_px, step_px, sink);
+            if (mode == 3) ldg4_probe_kernel<<<grid, block>>>(sink + 4, iters, stride_px, step_px, sink);
+            else if (mode == 4)
+                layout_probe_kernel<false><<<grid, block>>>(reinterpret_cast<const float4 *>(sink + 4), iters, stride_px, step_px, sink);
+            else if (mode == 5)
+                layout_probe_kernel<true><<<grid, block>>>(reinterpret_cast<const float4 *>(sink + 4), iters, stride_px, step_px, sink);
             else if (mode == 0) tex_probe_kernel<0><<<grid, block>>>(tex, iters, stride_px, step_px, sink);
             else if (mode == 1) tex_probe_kernel<1><<<grid, block>>>(tex, iters, stride_px, step_px, sink);
             else tex_probe_kernel<2><<<grid, block>>>(tex, iters, stride_px, step_px, sink);

@@ -20,7 +20,7 @@ from . import build as _build
 RCT_OK, RCT_EINVAL, RCT_ENOMEM, RCT_ECUDA, RCT_ESTATE, RCT_ETIMEOUT, RCT_ENOTSUP = range(7)
 RCT_PROJ_F32, RCT_PROJ_F16, RCT_PROJ_BF16 = 0, 1, 2
 RCT_INTERP_SOFT, RCT_INTERP_TEX = 0, 1
-RCT_GATHER_AUTO, RCT_GATHER_LDG, RCT_GATHER_TLD4, RCT_GATHER_MIX, RCT_GATHER_QUAD = 0, 1, 2, 3, 4
+RCT_GATHER_AUTO, RCT_GATHER_LDG, RCT_GATHER_TLD4, RCT_GATHER_MIX, RCT_GATHER_QUAD, RCT_GATHER_PAIR = 0, 1, 2, 3, 4, 5
 RCT_MAX_VIEWS_PER_PASS = 32
 STATUS_NAMES = {0: "RCT_OK", 1: "RCT_EINVAL", 2: "RCT_ENOMEM", 3: "RCT_ECUDA", 4: "RCT_ESTATE",
                 5: "RCT_ETIMEOUT", 6: "RCT_ENOTSUP"}

@@ -40,6 +40,8 @@ TUNINGS = [
     dict(gather=rct.RCT_GATHER_MIX, tex_zrun=5, views_per_pass=9, zrun=8, xvec=2, block_x=16, block_y=8),
     dict(gather=rct.RCT_GATHER_QUAD, views_per_pass=16, zrun=4, xvec=1, block_x=32, block_y=8),
     dict(gather=rct.RCT_GATHER_QUAD, views_per_pass=5, zrun=2, xvec=4, block_x=8, block_y=8),
+    dict(gather=rct.RCT_GATHER_PAIR, views_per_pass=16, zrun=8, xvec=1, block_x=16, block_y=8),
+    dict(gather=rct.RCT_GATHER_PAIR, views_per_pass=11, zrun=1, xvec=2, block_x=32, block_y=2),
 ]
 
 
@@ -64,7 +66,7 @@ def test_fp32_parity_xvec4(small_cases, case):
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
 @pytest.mark.parametrize("gather", [rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG, rct.RCT_GATHER_MIX,
-                                    rct.RCT_GATHER_QUAD])
+                                    rct.RCT_GATHER_QUAD, rct.RCT_GATHER_PAIR])
 def test_reduced_precision_storage_parity(small_cases, dtype, gather):
     """FP16/BF16 storage: same parity bar against the oracle fed the rounded projections."""
     w, proj, host = small_cases["L40"]
@@ -132,7 +134,8 @@ def test_split_calls_and_checkpoint_resume(small_cases, cuda_device):
 
 def test_host_input_path_matches_device_path(small_cases):
     w, proj, host = small_cases["L40"]
-    for gather in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG, rct.RCT_GATHER_MIX, rct.RCT_GATHER_QUAD):
+    for gather in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG, rct.RCT_GATHER_MIX, rct.RCT_GATHER_QUAD,
+                   rct.RCT_GATHER_PAIR):
         tun = dict(views_per_pass=5, gather=gather, zrun=4, tex_zrun=1)
         dev = gpu_backproject(w, proj, tuning=tun)
         pinned = torch.from_numpy(host).pin_memory()
@@ -184,7 +187,7 @@ def test_argument_errors(cuda_device):
         with pytest.raises(rct.RctError):
             rct.rct_backproject(bp.ctx, 0, 0, 2, None)
         for bad in [dict(views_per_pass=33), dict(zrun=3), dict(xvec=3), dict(block_x=7, block_y=1),
-                    dict(block_x=1024, block_y=1), dict(gather=9), dict(gather=5), dict(tex_zrun=9)]:
+                    dict(block_x=1024, block_y=1), dict(gather=9), dict(gather=6), dict(tex_zrun=9)]:
             with pytest.raises(rct.RctError):
                 bp.set_tuning(**bad)
         with pytest.raises(rct.RctError):
@@ -212,7 +215,7 @@ def test_all_gather_routes_agree_closely(small_cases):
     """Texture gather, plain loads and quad loads fetch the same taps; only the lerp's rounding differs."""
     w, proj, _ = small_cases["L64"]
     vols = {g: gpu_backproject(w, proj, tuning=dict(gather=g, zrun=4, xvec=1, views_per_pass=16))
-            for g in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG, rct.RCT_GATHER_QUAD)}
+            for g in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG, rct.RCT_GATHER_QUAD, rct.RCT_GATHER_PAIR)}
     ref = vols[rct.RCT_GATHER_LDG].astype(np.float64)
     for g, v in vols.items():
         rms, mx = rel_errors(v, ref)
