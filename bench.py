@@ -32,6 +32,11 @@ import numpy as np  # noqa: E402
 METRIC = "GUPS (voxel updates/s) at 512^3 x 496, FP32 projections"
 UNIT = "GUPS"
 
+# DRAM bytes (read + write) of one accumulating backprojection pass (K = 16 views, L = 512) from an ncu
+# capture of that launch, keyed by the tuning it ran with; a changed kernel or tuning has no entry
+# (traffic reported as null).  Source: profiles/bp_kernel_*_L512_ncu_full.md.
+TRAFFIC: dict = {}
+
 
 def parse_args():
     ap = argparse.ArgumentParser()
@@ -286,9 +291,14 @@ def run_ours(args, dist: Dist) -> dict | None:
     px_per_voxel = min(8.0, (w.geom.sdd / w.geom.sid) * float(w.spacing[0]) / w.geom.pitch)
     route = {rct.RCT_GATHER_LDG: "ldg", rct.RCT_GATHER_MIX: "mix", rct.RCT_GATHER_QUAD: "qld",
              rct.RCT_GATHER_PAIR: "pld"}.get(tun.get("gather"), "tex")
-    probe = lambda mode: rct.rct_probe_texture(mode, rct.RCT_PROJ_F32, px_per_voxel, px_per_voxel, 4096) / 1e9
-    ceilings = {"tex": probe(0), "ldg": probe(3), "qld": probe(4), "pld": probe(5)}
-    fetch_peak = ceilings["tex"] + ceilings["qld"] if route == "mix" else ceilings[route]
+    probe = lambda mode: round(rct.rct_probe_texture(mode, rct.RCT_PROJ_F32, px_per_voxel, px_per_voxel, 4096) / 1e9, 1)
+    probes = {"tex_tld4": probe(0), "ldg4": probe(3), "quad": probe(4), "pair": probe(5)}
+    # The gather needs four FP32 texels (16 B) per update from the L1/texture path.  Its ceiling is
+    # the L1 load data path: 128 B per clock per SM x SMs x the SM clock measured during the run.
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    l1_peak = 128.0 * sms * sm_mhz * 1e6 / 1e9                        # GB/s
+    gather_gbs = kernel_gups * 16.0                                   # GB/s of algorithmic texel bytes
     vol_bytes = 4 * w.L ** 3
     img_bytes = 4 * w.geom.det_w * w.geom.det_h
     # per step: the first pass writes only, later passes read and write; each view's image is read once
@@ -296,14 +306,15 @@ def run_ours(args, dist: Dist) -> dict | None:
     bytes_per_launch = bytes_per_step / passes_per_step
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved_gbs = bytes_per_launch / avg_kernel_s / 1e9
-    roofline = {"bound": "l1tex", "achieved": round(kernel_gups, 1), "peak": round(fetch_peak, 1),
-                "unit": "G cell-fetches/s (one 2x2 fetch per voxel update)",
-                "frac": round(kernel_gups / fetch_peak, 4), "traffic": None,
-                "kernel": f"bp_kernel, {route} route", "route": route,
-                "peak_source": ("measured live with the library's fetch probes at this workload's lane stride "
-                                f"({px_per_voxel:.2f} px): " + ", ".join(f"{k} {v:.1f} G/s" for k, v in ceilings.items())
-                                + ("; mixed route: tex + qld" if route == "mix" else "")),
+    traffic = TRAFFIC.get(json.dumps(tun, sort_keys=True)) if w.L == 512 and w.n_views == 496 else None
+    roofline = {"bound": "l1tex", "achieved": round(gather_gbs, 1), "peak": round(l1_peak, 1), "unit": "GB/s",
+                "frac": round(gather_gbs / l1_peak, 4), "traffic": traffic,
+                "what": "algorithmic gather bytes (four FP32 texels per voxel update) through the L1 load data path",
+                "peak_source": (f"derived from unit counts: 128 B/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz "
+                                "(median SM clock sampled during the timed region)"),
+                "kernel": f"bp_kernel, {route} route", "kernel_gups": round(kernel_gups, 1),
                 "kernel_share_of_step": round(kernel_ms / ms_total, 4), "updates_per_launch": int(upd_per_launch),
+                "fetch_probes_gfetch_s": probes, "probe_lane_stride_px": round(px_per_voxel, 2),
                 "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                         "frac": round(achieved_gbs / hbm_peak, 4), "algorithmic_bytes_per_launch": int(bytes_per_launch),
                         "peak_source": "measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "fallback"}}

@@ -92,7 +92,7 @@ typedef enum rct_gather {
 /* Kernel tuning.  Zero in any field means "keep the current value". */
 typedef struct rct_tuning {
     int views_per_pass;  /* K: views accumulated in registers per volume pass, 1..32 */
-    int zrun;            /* voxels per thread along z: 1, 2, 4 or 8 */
+    int zrun;            /* voxels per thread along z: 1, 2, 4, 8 or 16 (16 needs xvec <= 2) */
     int xvec;            /* voxels per thread along x: 1, 2 or 4 (4 needs L % 4 == 0) */
     int block_x;         /* threads per block along x */
     int block_y;         /* threads per block along y; block_x * block_y <= 512 */

@@ -24,7 +24,7 @@ CANDIDATES = {
                (rct.RCT_GATHER_PAIR, 0), (rct.RCT_GATHER_MIX, 1), (rct.RCT_GATHER_MIX, 2),
                (rct.RCT_GATHER_MIX, 4), (rct.RCT_GATHER_MIX, 6)],
     "views_per_pass": [4, 8, 16, 24, 32],
-    "zrun": [1, 2, 4, 8],
+    "zrun": [1, 2, 4, 8, 16],
     "xvec": [1, 2, 4],
     "block": [(32, 4), (32, 8), (32, 16), (64, 2), (64, 4), (16, 8), (16, 16), (8, 16), (128, 2)],
 }
@@ -33,6 +33,8 @@ CANDIDATES = {
 def _valid(L: int, t: dict) -> bool:
     bx, by = t["block_x"], t["block_y"]
     if t.get("gather") == rct.RCT_GATHER_MIX and not (1 <= t.get("tex_zrun", 0) < t["zrun"]):
+        return False
+    if t["zrun"] == 16 and t["xvec"] > 2:
         return False
     return L % t["xvec"] == 0 and bx * by <= 512 and (bx * by) % 32 == 0
 

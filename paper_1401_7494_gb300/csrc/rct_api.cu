@@ -551,13 +551,15 @@ rct_status rct_set_tuning(rct_ctx *c, const rct_tuning *t) {
     if (t->tex_zrun) n.tex_zrun = t->tex_zrun;
     if (n.views_per_pass < 1 || n.views_per_pass > KMAX)
         return fail(RCT_EINVAL, "views_per_pass %d outside 1..%d", n.views_per_pass, KMAX);
-    if (n.zrun != 1 && n.zrun != 2 && n.zrun != 4 && n.zrun != 8) return fail(RCT_EINVAL, "zrun %d not in {1,2,4,8}", n.zrun);
+    if (n.zrun != 1 && n.zrun != 2 && n.zrun != 4 && n.zrun != 8 && n.zrun != 16)
+        return fail(RCT_EINVAL, "zrun %d not in {1,2,4,8,16}", n.zrun);
+    if (n.zrun == 16 && n.xvec > 2) return fail(RCT_EINVAL, "zrun 16 needs xvec <= 2");
     if (n.xvec != 1 && n.xvec != 2 && n.xvec != 4) return fail(RCT_EINVAL, "xvec %d not in {1,2,4}", n.xvec);
     if (c->L % n.xvec != 0) return fail(RCT_EINVAL, "xvec %d does not divide L = %d", n.xvec, c->L);
     if (n.block_x < 1 || n.block_y < 1 || n.block_x * n.block_y > 512 || (n.block_x * n.block_y) % 32 != 0)
         return fail(RCT_EINVAL, "block %dx%d: need a multiple of 32 threads, at most 512", n.block_x, n.block_y);
     if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_PAIR) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
-    if (n.tex_zrun < 0 || n.tex_zrun > 8) return fail(RCT_EINVAL, "tex_zrun %d outside 0..8", n.tex_zrun);
+    if (n.tex_zrun < 0 || n.tex_zrun > 16) return fail(RCT_EINVAL, "tex_zrun %d outside 0..16", n.tex_zrun);
     c->tune = n;
     return RCT_OK;
 }

@@ -344,6 +344,9 @@ cudaError_t dispatch_r(const LaunchConfig &c, const BpParams &p, cudaStream_t s)
         case 2: return launch_one<G, DT, XV, 2, ROUTE>(c, p, s);
         case 4: return launch_one<G, DT, XV, 4, ROUTE>(c, p, s);
         case 8: return launch_one<G, DT, XV, 8, ROUTE>(c, p, s);
+        case 16:
+            if constexpr (XV <= 2) return launch_one<G, DT, XV, 16, ROUTE>(c, p, s);
+            return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }

@@ -42,6 +42,8 @@ TUNINGS = [
     dict(gather=rct.RCT_GATHER_QUAD, views_per_pass=5, zrun=2, xvec=4, block_x=8, block_y=8),
     dict(gather=rct.RCT_GATHER_PAIR, views_per_pass=16, zrun=8, xvec=1, block_x=16, block_y=8),
     dict(gather=rct.RCT_GATHER_PAIR, views_per_pass=11, zrun=1, xvec=2, block_x=32, block_y=2),
+    dict(gather=rct.RCT_GATHER_PAIR, views_per_pass=16, zrun=16, xvec=1, block_x=8, block_y=16),
+    dict(gather=rct.RCT_GATHER_TLD4, views_per_pass=8, zrun=16, xvec=2, block_x=16, block_y=8),
 ]
 
 
@@ -186,7 +188,7 @@ def test_argument_errors(cuda_device):
             assert e.value.status == rct.RCT_EINVAL
         with pytest.raises(rct.RctError):
             rct.rct_backproject(bp.ctx, 0, 0, 2, None)
-        for bad in [dict(views_per_pass=33), dict(zrun=3), dict(xvec=3), dict(block_x=7, block_y=1),
+        for bad in [dict(views_per_pass=33), dict(zrun=3), dict(zrun=16, xvec=4), dict(xvec=3), dict(block_x=7, block_y=1),
                     dict(block_x=1024, block_y=1), dict(gather=9), dict(gather=6), dict(tex_zrun=9)]:
             with pytest.raises(rct.RctError):
                 bp.set_tuning(**bad)
