@@ -61,3 +61,33 @@ def test_sampled_parity_large(cuda_device, name, dtype):
     del vol
     ref = _sampled_reference(w, oracle_inputs(host, dtype), idx)
     assert_parity(got, ref, f"{name} {dtype} sampled ({idx.size} voxels)")
+
+
+def test_maximum_volume_L2048(cuda_device):
+    """The largest volume the library accepts (2048^3 FP32 = 32 GiB), a few full-size views."""
+    w = synth.make_workload(2048, n_views=8, seed=1408)
+    proj = w.projections(device=cuda_device)
+    host = proj.cpu().numpy()
+    tun = tuning_mod.lookup(w.L, "f32", "soft")
+    stream = torch.cuda.current_stream()
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(**tun)
+        bp.backproject(proj, 0, w.n_views, stream)
+        dev_vol = torch.empty((w.L,) * 3, dtype=torch.float32, device=cuda_device)
+        bp.read_volume(dev_vol, stream)
+        torch.cuda.synchronize()
+    idx = _sample_indices(w.L, seed=w.seed, n_random=1 << 14, planes=(w.L // 2,))
+    got = dev_vol.view(-1)[torch.from_numpy(idx).to(cuda_device)].cpu().numpy()
+    del dev_vol
+    ref = _sampled_reference(w, host, idx)
+    assert_parity(got, ref, f"L=2048 sampled ({idx.size} voxels)")
+
+
+def test_large_detector(cuda_device):
+    """A 4096 x 3072 detector (12.6 Mpx per view) through every gather route."""
+    w = synth.make_workload(48, n_views=6, det_w=4096, det_h=3072, seed=1409)
+    proj = w.projections(device=cuda_device)
+    ref = oracle_volume(w, proj.cpu().numpy())
+    for g in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_PAIR, rct.RCT_GATHER_QUAD, rct.RCT_GATHER_LDG):
+        got = gpu_backproject(w, proj, tuning=dict(gather=g, views_per_pass=4))
+        assert_parity(got, ref, f"4096x3072 detector, gather {g}")

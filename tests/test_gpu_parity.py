@@ -189,7 +189,7 @@ def test_argument_errors(cuda_device):
         with pytest.raises(rct.RctError):
             rct.rct_backproject(bp.ctx, 0, 0, 2, None)
         for bad in [dict(views_per_pass=33), dict(zrun=3), dict(zrun=16, xvec=4), dict(xvec=3), dict(block_x=7, block_y=1),
-                    dict(block_x=1024, block_y=1), dict(gather=9), dict(gather=6), dict(tex_zrun=9)]:
+                    dict(block_x=1024, block_y=1), dict(gather=9), dict(gather=6), dict(tex_zrun=17)]:
             with pytest.raises(rct.RctError):
                 bp.set_tuning(**bad)
         with pytest.raises(rct.RctError):
