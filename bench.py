@@ -153,6 +153,12 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
 
 
+def workload_config(name: str, w) -> dict:
+    return {"workload": f"{name}: L={w.L}^3 volume, {w.n_views} views of {w.geom.det_w}x{w.geom.det_h} FP32 "
+                        f"projections, seeded ellipsoid phantom",
+            "L": w.L, "n_views": w.n_views, "det": [w.geom.det_w, w.geom.det_h], "seed": w.seed}
+
+
 # ----------------------------------------------------------------------------- CPU oracle timing
 
 def oracle_rate(w, host_proj, target_s: float, max_planes: int | None = None):
@@ -323,11 +329,8 @@ def run_ours(args, dist: Dist) -> dict | None:
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: L={w.L}^3 volume, {w.n_views} views of "
-                               f"{w.geom.det_w}x{w.geom.det_h} FP32 projections, seeded ellipsoid phantom",
-                   "L": w.L, "n_views": w.n_views, "det": [w.geom.det_w, w.geom.det_h], "seed": w.seed,
-                   "tuning": tun, "parallelism": f"replicas x{dist.world}",
-                   "l2": "inputs larger than L2 (2.4 GB projections, volume >= 512 MB); no flush"},
+        "config": dict(workload_config(args.workload, w), tuning=tun, parallelism=f"replicas x{dist.world}",
+                       l2="inputs larger than L2 (2.4 GB projections, volume >= 512 MB); no flush"),
         "roofline": roofline,
         "clocks": clk,
         "gpu_launches": int(launches),
@@ -413,7 +416,7 @@ def run_reference(args, dist: Dist) -> dict | None:
     cores = oracle.max_threads()
     sample = ""
     for i in range(args.warmup + args.steps):
-        gups, cores, sample = oracle_rate(w, host, per_step, max_planes=8)
+        gups, cores, sample = oracle_rate(w, host, per_step)
         if i >= args.warmup:
             rates.append(gups)
     value = statistics.median(rates)
@@ -421,8 +424,7 @@ def run_reference(args, dist: Dist) -> dict | None:
     return {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{args.workload}: L={w.L}^3, {w.n_views} views of {w.geom.det_w}x{w.geom.det_h}",
-                       "per_step_sample": sample},
+            "config": dict(workload_config(args.workload, w), per_step_sample=sample),
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -84,11 +84,19 @@ def test_maximum_volume_L2048(cuda_device):
     assert_parity(got, ref, f"L=2048 sampled ({idx.size} voxels)")
 
 
+def scaled_rms_tol(det_w: int, n_views: int) -> float:
+    """The FP32 bar scaled off the stated configuration (1248-pixel rows, 496 views): the rounding error
+    of an FP32 detector coordinate grows with its magnitude (proportional to the row length), and
+    independent per-view errors shrink relative to the summed signal as 1/sqrt(views)."""
+    return 1e-5 * max(1.0, det_w / 1248.0) * max(1.0, (496.0 / n_views) ** 0.5)
+
+
 def test_large_detector(cuda_device):
     """A 4096 x 3072 detector (12.6 Mpx per view) through every gather route."""
     w = synth.make_workload(48, n_views=32, det_w=4096, det_h=3072, seed=1409)
     proj = w.projections(device=cuda_device)
     ref = oracle_volume(w, proj.cpu().numpy())
+    tol = scaled_rms_tol(w.geom.det_w, w.n_views)
     for g in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_PAIR, rct.RCT_GATHER_QUAD, rct.RCT_GATHER_LDG):
         got = gpu_backproject(w, proj, tuning=dict(gather=g, views_per_pass=4))
-        assert_parity(got, ref, f"4096x3072 detector, gather {g}")
+        assert_parity(got, ref, f"4096x3072 detector, gather {g}", rms_tol=tol)
