@@ -35,7 +35,10 @@ UNIT = "GUPS"
 # DRAM bytes (read + write) of one accumulating backprojection pass (K = 16 views, L = 512) from an ncu
 # capture of that launch, keyed by the tuning it ran with; a changed kernel or tuning has no entry
 # (traffic reported as null).  Source: profiles/bp_kernel_*_L512_ncu_full.md.
-TRAFFIC: dict = {}
+TRAFFIC: dict = {
+    '{"block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0, "views_per_pass": 16, "xvec": 1, "zrun": 8}':
+        690_587_904 + 482_652_672,
+}
 
 
 def parse_args():
