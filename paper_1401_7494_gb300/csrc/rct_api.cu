@@ -51,16 +51,17 @@ struct Slot {
 
 void rct::set_view_geometry(ViewParams *vp, const double fold[12], int cu, int cv) {
     for (int k = 0; k < 4; ++k) {
-        vp->muv[2 * k] = static_cast<float>(fold[k]);          // u' row
-        vp->muv[2 * k + 1] = static_cast<float>(fold[4 + k]);  // v' row
-        vp->mw[k] = static_cast<float>(fold[8 + k]);
+        const double u = fold[k], v = fold[4 + k], w = fold[8 + k];
+        const float uh = static_cast<float>(u), vh = static_cast<float>(v), wh = static_cast<float>(w);
+        vp->muv[2 * k] = uh;                                        // u' row
+        vp->muv[2 * k + 1] = vh;                                    // v' row
+        vp->mw[k] = wh;
+        vp->muv_lo[2 * k] = static_cast<float>(u - static_cast<double>(uh));
+        vp->muv_lo[2 * k + 1] = static_cast<float>(v - static_cast<double>(vh));
+        vp->mw_lo[k] = static_cast<float>(w - static_cast<double>(wh));
     }
     vp->cu = cu;
     vp->cv = cv;
-    vp->gofs_x = -(12582912.0f - static_cast<float>(cu + 1));   // 1.5 * 2^23, the kernel's floor constant
-    vp->gofs_y = -(12582912.0f - static_cast<float>(cv + 1));
-    vp->qcx = 0x4B400000 - cu - 1;
-    vp->qcy = 0x4B400000 - cv - 1;
 }
 
 rct_status rct::rct_internal_fail(rct_status code, const char *fmt, ...) {

@@ -49,6 +49,18 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// Double-float accumulation: adds (h + l) * d to the unevaluated sum s + e, with the exact
+// product error (FMA) and the exact addition error (two-sum) kept in e.
+__device__ __forceinline__ void df_add_term(float h, float l, float d, float &s, float &e) {
+    const float p = h * d;
+    const float pe = fmaf(h, d, -p);
+    const float t = s + p;
+    const float bb = t - s;
+    const float se = (s - (t - bb)) + (p - bb);
+    s = t;
+    e += se + fmaf(l, d, pe);
+}
+
 template <int DT>
 __device__ __forceinline__ float load_px(const void *img, ptrdiff_t off) {
     if constexpr (DT == DT_F32) {
@@ -214,26 +226,34 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
     const size_t plane = static_cast<size_t>(L) * L;
     float *vb = p.vol + static_cast<size_t>(z0) * plane + static_cast<size_t>(y) * L + x0;
 
+    // The volume is touched once per pass: streaming (evict-first) loads and stores keep it from
+    // displacing the projection data the gathers reuse in L1 and L2.
     float acc[R][XV];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const bool live = p.accumulate && (z0 + r < L);
         if constexpr (XV == 4) {
             float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (live) t = *reinterpret_cast<const float4 *>(vb + r * plane);
+            if (live) t = __ldcs(reinterpret_cast<const float4 *>(vb + r * plane));
             acc[r][0] = t.x; acc[r][1] = t.y; acc[r][2] = t.z; acc[r][3] = t.w;
         } else if constexpr (XV == 2) {
             float2 t = make_float2(0.f, 0.f);
-            if (live) t = *reinterpret_cast<const float2 *>(vb + r * plane);
+            if (live) t = __ldcs(reinterpret_cast<const float2 *>(vb + r * plane));
             acc[r][0] = t.x; acc[r][1] = t.y;
         } else {
-            acc[r][0] = live ? vb[r * plane] : 0.0f;
+            acc[r][0] = live ? __ldcs(vb + r * plane) : 0.0f;
         }
     }
 
     const float xc0 = static_cast<float>(x0) - p.cen;
     const float yc = static_cast<float>(y) - p.cen;
     const float zc0 = static_cast<float>(z0) - p.cen;
+    // the block's first voxel (centred coordinates, exact) and this thread's offset from it
+    const float bX = static_cast<float>(blockIdx.x * blockDim.x * XV) - p.cen;
+    const float bY = static_cast<float>(blockIdx.y * blockDim.y) - p.cen;
+    const float bZ = zc0;
+    const float lx = static_cast<float>(threadIdx.x * XV);
+    const float ly = static_cast<float>(threadIdx.y);
     const int tex_zrun = p.tex_zrun;   // z positions [0, tex_zrun) use the texture route
 
 #pragma unroll 1
@@ -241,23 +261,51 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
         const ViewParams &v = p.view[k];
         const float2 *muv = reinterpret_cast<const float2 *>(v.muv);
         const float *mw = v.mw;
-        // Part 1 at the thread's first voxel; (u', v') travel as one f32x2 pair.
-        const float2 buv = __ffma2_rn(make_float2(xc0, xc0), muv[0],
-                                      __ffma2_rn(make_float2(yc, yc), muv[1],
-                                                 __ffma2_rn(make_float2(zc0, zc0), muv[2], muv[3])));
-        const float bw = fmaf(mw[0], xc0, fmaf(mw[1], yc, fmaf(mw[2], zc0, mw[3])));
         ViewConsts c;
         c.m_z = muv[2];
         c.w_z = mw[2];
-        c.cu = v.cu;
-        c.cv = v.cv;
-        c.gofs = make_float2(v.gofs_x, v.gofs_y);
-        c.qcx = v.qcx;
-        c.qcy = v.qcy;
         c.tex = static_cast<cudaTextureObject_t>(v.tex);
         c.img = v.img;
         c.quad = v.quad;
         const float2 m_x = muv[0];
+        float2 buv;
+        float bw;
+        if constexpr (G == G_SOFT) {
+            // Block frame: (u', v', w) at the block's first voxel in double-float (uniform across the
+            // block), minus a block-local integer pixel shift; threads add short local offsets.
+            const float *hu = v.muv, *lu = v.muv_lo;
+            float su = hu[6], eu = lu[6], sv = hu[7], ev = lu[7], sw = mw[3], ew = v.mw_lo[3];
+            df_add_term(hu[0], lu[0], bX, su, eu);
+            df_add_term(hu[2], lu[2], bY, su, eu);
+            df_add_term(hu[4], lu[4], bZ, su, eu);
+            df_add_term(hu[1], lu[1], bX, sv, ev);
+            df_add_term(hu[3], lu[3], bY, sv, ev);
+            df_add_term(hu[5], lu[5], bZ, sv, ev);
+            df_add_term(mw[0], v.mw_lo[0], bX, sw, ew);
+            df_add_term(mw[1], v.mw_lo[1], bY, sw, ew);
+            df_add_term(mw[2], v.mw_lo[2], bZ, sw, ew);
+            const float wb = sw + ew;
+            const float rb = rcp_approx(wb);
+            const float cub = rintf((su + eu) * rb);                        // any nearby integer will do
+            const float cvb = rintf((sv + ev) * rb);
+            const float pu = cub * sw, pv = cvb * sw;
+            const float tu = (su - pu) + ((eu - fmaf(cub, sw, -pu)) - cub * ew);   // u'(corner) - cub * w(corner)
+            const float tv = (sv - pv) + ((ev - fmaf(cvb, sw, -pv)) - cvb * ew);
+            c.cu = v.cu + static_cast<int>(cub);
+            c.cv = v.cv + static_cast<int>(cvb);
+            c.gofs = make_float2(-(kMagic - static_cast<float>(c.cu + 1)), -(kMagic - static_cast<float>(c.cv + 1)));
+            c.qcx = kMagicBits - c.cu - 1;
+            c.qcy = kMagicBits - c.cv - 1;
+            buv = __ffma2_rn(make_float2(lx, lx), muv[0], __ffma2_rn(make_float2(ly, ly), muv[1], make_float2(tu, tv)));
+            bw = fmaf(mw[0], lx, fmaf(mw[1], ly, wb));
+        } else {
+            // Texture-unit filtering needs absolute texture coordinates: the plain centred frame.
+            buv = __ffma2_rn(make_float2(xc0, xc0), muv[0],
+                             __ffma2_rn(make_float2(yc, yc), muv[1], __ffma2_rn(make_float2(zc0, zc0), muv[2], muv[3])));
+            bw = fmaf(mw[0], xc0, fmaf(mw[1], yc, fmaf(mw[2], zc0, mw[3])));
+            c.cu = v.cu;
+            c.cv = v.cv;
+        }
         if constexpr (G == G_SOFT) {
             // Clipping per run (the paper's clipping mask, Section "Implementation"): the
             // thread's voxels form a segment (XV = 1) or parallelogram in (x, z); its projection
@@ -319,12 +367,11 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
     for (int r = 0; r < R; ++r) {
         if (z0 + r >= L) break;
         if constexpr (XV == 4) {
-            *reinterpret_cast<float4 *>(vb + r * plane) =
-                make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+            __stcs(reinterpret_cast<float4 *>(vb + r * plane), make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]));
         } else if constexpr (XV == 2) {
-            *reinterpret_cast<float2 *>(vb + r * plane) = make_float2(acc[r][0], acc[r][1]);
+            __stcs(reinterpret_cast<float2 *>(vb + r * plane), make_float2(acc[r][0], acc[r][1]));
         } else {
-            vb[r * plane] = acc[r][0];
+            __stcs(vb + r * plane, acc[r][0]);
         }
     }
 }

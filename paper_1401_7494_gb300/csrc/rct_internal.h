@@ -27,15 +27,17 @@ enum DType : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 // centre projects -- keeps u' and v' small, so FP32 rounding of the
 // coordinates stays close to one rounding of the final pixel position.
 //
-// With t = 1.5 * 2^23 + floor(q) (the directed-rounding add in the kernel), the cell's
-// column i0 = cu + floor(q.x); the host precomputes the constants that turn t into the texture
-// gather coordinate (gofs) and into the padded quad index (qcx, qcy).
+// The matrix is split into FP32 high parts and the FP32 rounding of the remainders (low parts):
+// a block evaluates its corner's (u', v', w) once per view in double-float arithmetic from both,
+// picks a block-local integer shift, and its threads then work with small local coordinates, so the
+// FP32 pixel coordinate is accurate to a few units in the last place of a short local distance
+// wherever the block sits on the detector.
 struct ViewParams {
-    float muv[8];              // rows u', v' interleaved: (m0, m4), (m1, m5), (m2, m6), (m3, m7)
-    float mw[4];               // row w
-    int cu, cv;                // integer detector shift (0 for texture-filtered sampling)
-    float gofs_x, gofs_y;      // t + gofs = (i0 + 1, j0 + 1): the exact gather corner
-    int qcx, qcy;              // bits(t) - qc = (i0 + 1, j0 + 1): the padded quad index
+    float muv[8];              // rows u', v' interleaved, high parts: (m0, m4), (m1, m5), (m2, m6), (m3, m7)
+    float mw[4];               // row w, high parts
+    float muv_lo[8];           // low parts, same order
+    float mw_lo[4];
+    int cu, cv;                // integer detector shift of the fold (0 for texture-filtered sampling)
     unsigned long long tex;    // cudaTextureObject_t (gather or filtered texture)
     const void *img;           // linear image, H x W, row-major (plain loads)
     const void *quad;          // staged quad or pair image, zero padded (quad / pair loads)
