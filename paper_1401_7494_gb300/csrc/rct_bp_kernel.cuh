@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
         c.tex = static_cast<cudaTextureObject_t>(v.tex);
         c.img = v.img;
         c.quad = v.quad;
-        const float2 m_x = muv[0];
+        float2 m_x = muv[0];
         float2 buv;
         float bw;
         if constexpr (G == G_SOFT) {
@@ -296,7 +296,12 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
             c.gofs = make_float2(-(kMagic - static_cast<float>(c.cu + 1)), -(kMagic - static_cast<float>(c.cv + 1)));
             c.qcx = kMagicBits - c.cu - 1;
             c.qcy = kMagicBits - c.cv - 1;
-            buv = __ffma2_rn(make_float2(lx, lx), muv[0], __ffma2_rn(make_float2(ly, ly), muv[1], make_float2(tu, tv)));
+            // the shift scales with each voxel's own w: the local rows are (u' - cub w, v' - cvb w)
+            const float2 nshift = make_float2(-cub, -cvb);
+            m_x = __ffma2_rn(nshift, make_float2(mw[0], mw[0]), muv[0]);
+            const float2 m_y = __ffma2_rn(nshift, make_float2(mw[1], mw[1]), muv[1]);
+            c.m_z = __ffma2_rn(nshift, make_float2(mw[2], mw[2]), muv[2]);
+            buv = __ffma2_rn(make_float2(lx, lx), m_x, __ffma2_rn(make_float2(ly, ly), m_y, make_float2(tu, tv)));
             bw = fmaf(mw[0], lx, fmaf(mw[1], ly, wb));
         } else {
             // Texture-unit filtering needs absolute texture coordinates: the plain centred frame.
