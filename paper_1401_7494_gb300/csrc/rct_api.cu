@@ -51,17 +51,28 @@ struct Slot {
 
 void rct::set_view_geometry(ViewParams *vp, const double fold[12], int cu, int cv) {
     for (int k = 0; k < 4; ++k) {
-        const double u = fold[k], v = fold[4 + k], w = fold[8 + k];
-        const float uh = static_cast<float>(u), vh = static_cast<float>(v), wh = static_cast<float>(w);
-        vp->muv[2 * k] = uh;                                        // u' row
-        vp->muv[2 * k + 1] = vh;                                    // v' row
-        vp->mw[k] = wh;
-        vp->muv_lo[2 * k] = static_cast<float>(u - static_cast<double>(uh));
-        vp->muv_lo[2 * k + 1] = static_cast<float>(v - static_cast<double>(vh));
-        vp->mw_lo[k] = static_cast<float>(w - static_cast<double>(wh));
+        vp->muv[2 * k] = static_cast<float>(fold[k]);          // u' row
+        vp->muv[2 * k + 1] = static_cast<float>(fold[4 + k]);  // v' row
+        vp->mw[k] = static_cast<float>(fold[8 + k]);
     }
     vp->cu = cu;
     vp->cv = cv;
+}
+
+void rct::set_view_geo(ViewGeo *vg, const double fold[12], int cu, int cv) {
+    for (int k = 0; k < 4; ++k) {
+        const double u = fold[k], v = fold[4 + k], w = fold[8 + k];
+        const float uh = static_cast<float>(u), vh = static_cast<float>(v), wh = static_cast<float>(w);
+        vg->hu[2 * k] = uh;
+        vg->hu[2 * k + 1] = vh;
+        vg->hw[k] = wh;
+        vg->lu[2 * k] = static_cast<float>(u - static_cast<double>(uh));
+        vg->lu[2 * k + 1] = static_cast<float>(v - static_cast<double>(vh));
+        vg->lw[k] = static_cast<float>(w - static_cast<double>(wh));
+    }
+    vg->cu = cu;
+    vg->cv = cv;
+    vg->pad_[0] = vg->pad_[1] = 0;
 }
 
 rct_status rct::rct_internal_fail(rct_status code, const char *fmt, ...) {
@@ -81,6 +92,7 @@ struct rct_ctx {
     bool vol_zero_pending = true;   // the volume is logically zero; the next pass overwrites
 
     bool geometry_set = false;
+    ViewGeo *geo_dev = nullptr;     // n_views block-frame geometries on the device
     std::vector<double> fold;       // n_views x 12, FP64: rows u', v', w over centred voxel coords
     std::vector<int> shift;         // n_views x 2: integer detector shift (cu, cv)
 
@@ -303,6 +315,7 @@ void init_params(const rct_ctx *c, BpParams *p) {
     p->cen = 0.5f * (c->L - 1);
     p->tex_zrun = tex_zrun_of(c);
     p->quad = load_layout(c);
+    p->geo = c->geo_dev;
 }
 
 // FP32 view parameters for one view and kernel kind, from the FP64 fold.
@@ -507,6 +520,7 @@ void rct_destroy(rct_ctx *c) {
     if (c->vol) cudaFree(c->vol);
     if (c->lin_stage) cudaFree(c->lin_stage);
     if (c->quad_buf) cudaFree(c->quad_buf);
+    if (c->geo_dev) cudaFree(c->geo_dev);
     if (c->widen_buf) cudaFree(c->widen_buf);
     for (int i = 0; i < 2; ++i) {
         if (c->ev_filled[i]) cudaEventDestroy(c->ev_filled[i]);
@@ -525,6 +539,23 @@ rct_status rct_set_geometry(rct_ctx *c, const double *matrices, const double ori
     std::vector<int> shift(2 * (size_t)c->n_views);
     rct_status st = rct_fold_geometry(c->L, c->n_views, matrices, origin, spacing, fold.data(), shift.data());
     if (st != RCT_OK) return st;
+    if ((st = check_ctx(c))) return st;
+    std::vector<ViewGeo> geo(c->n_views);
+    for (int v = 0; v < c->n_views; ++v) set_view_geo(&geo[v], &fold[12 * (size_t)v], shift[2 * v], shift[2 * v + 1]);
+    if (!c->geo_dev) {
+        cudaError_t e = cudaMalloc(&c->geo_dev, sizeof(ViewGeo) * c->n_views);
+        if (e != cudaSuccess) {
+            c->geo_dev = nullptr;
+            return fail(RCT_ENOMEM, "geometry table allocation failed");
+        }
+    }
+    // Passes already queued with a previous geometry read the block-frame table when they run:
+    // let them finish before it is overwritten (a fresh context has none).
+    if (c->launches > 0) RCT_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    if ((st = ensure_copy_machinery(c))) return st;
+    RCT_CUDA(cudaMemcpyAsync(c->geo_dev, geo.data(), sizeof(ViewGeo) * c->n_views, cudaMemcpyHostToDevice,
+                             c->copy_stream), "cudaMemcpyAsync(geometry)");
+    RCT_CUDA(cudaStreamSynchronize(c->copy_stream), "cudaStreamSynchronize");
     c->fold.swap(fold);
     c->shift.swap(shift);
     c->geometry_set = true;
@@ -621,6 +652,7 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
         const int g = batch & 1;
         const int kb = std::min(K, n - b);
         p.K = kb;
+        p.first_view = first_view + b;
         p.accumulate = c->vol_zero_pending ? 0 : 1;
         if (staged) RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[g], 0), "cudaStreamWaitEvent");
         for (int k = 0; k < kb; ++k) {
@@ -681,6 +713,7 @@ rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, 
         // copy stream: wait until group g's previous pass is done, then fill it
         RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[g], 0), "cudaStreamWaitEvent");
         p.K = kb;
+        p.first_view = first_view + b;
         p.accumulate = c->vol_zero_pending ? 0 : 1;
         for (int k = 0; k < kb; ++k) {
             const void *src = base + (size_t)(b + k) * view_bytes;

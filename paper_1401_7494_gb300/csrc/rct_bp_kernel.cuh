@@ -118,18 +118,15 @@ __device__ __forceinline__ void accumulate_tex(const ViewConsts &c, float2 q, fl
     acc = fmaf(fmaf(f.y, t1 - t0, t0), w2, acc);
 }
 
-// Part 2 + 3 by one load of the staged quad element (see ViewParams).  A cell with no tap on the
-// image has no element; such a lane loads element 0 and adds it with weight 0.
+// Part 2 + 3 by one load of the staged quad element (see ViewParams).  The unsigned cell index is
+// clamped to the image's all-zero last row / column: a cell with no tap on the image adds 0.
 template <int DT>
 __device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 q, float w2, int W, int H,
                                                 float &acc) {
     const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));
-    const int ix = __float_as_int(t.x) - c.qcx;                             // padded index (i0 + 1, j0 + 1)
-    const int jy = __float_as_int(t.y) - c.qcy;
-    const bool on = static_cast<unsigned>(ix) <= static_cast<unsigned>(W) &&
-                    static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
-    const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 1) + static_cast<unsigned>(ix) : 0u;
-    w2 = on ? w2 : 0.0f;
+    const unsigned ix = min(static_cast<unsigned>(__float_as_int(t.x) - c.qcx), static_cast<unsigned>(W + 1));
+    const unsigned jy = min(static_cast<unsigned>(__float_as_int(t.y) - c.qcy), static_cast<unsigned>(H + 1));
+    const unsigned e = jy * static_cast<unsigned>(W + 2) + ix;
     float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
     if constexpr (DT == DT_F32) {
         const float4 v = __ldg(static_cast<const float4 *>(c.quad) + e);
@@ -153,17 +150,14 @@ __device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 q, f
 }
 
 // Part 2 + 3 by two loads of consecutive staged vertical pairs (see ViewParams): neighbouring
-// lanes share cache sectors, so less data moves from L2 than with quads.  Same off-image rule.
+// lanes share cache sectors, so less data moves from L2 than with quads.  Same clamp as quads.
 template <int DT>
 __device__ __forceinline__ void accumulate_pair(const ViewConsts &c, float2 q, float w2, int W, int H,
                                                 float &acc) {
     const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));
-    const int ix = __float_as_int(t.x) - c.qcx;                             // padded index (i0 + 1, j0 + 1)
-    const int jy = __float_as_int(t.y) - c.qcy;
-    const bool on = static_cast<unsigned>(ix) <= static_cast<unsigned>(W) &&
-                    static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
-    const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 2) + static_cast<unsigned>(ix) : 0u;
-    w2 = on ? w2 : 0.0f;
+    const unsigned ix = min(static_cast<unsigned>(__float_as_int(t.x) - c.qcx), static_cast<unsigned>(W + 1));
+    const unsigned jy = min(static_cast<unsigned>(__float_as_int(t.y) - c.qcy), static_cast<unsigned>(H + 1));
+    const unsigned e = jy * static_cast<unsigned>(W + 3) + ix;
     float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
     if constexpr (DT == DT_F32) {
         const float2 *pp = static_cast<const float2 *>(c.quad) + e;
@@ -216,12 +210,60 @@ __device__ __forceinline__ int2 cell_index(const ViewConsts &c, float2 uv, float
     return make_int2(__float_as_int(t.x) - c.qcx, __float_as_int(t.y) - c.qcy);
 }
 
+// Block frame of one view (see ViewGeo): the block corner's (u', v', w) in double-float, a
+// block-local integer pixel shift (cub, cvb), and the rows with the shift applied.  Stored as three
+// float4: (tu, tv, wb, bits(cu)), (mx.u, mx.v, my.u, my.v), (mz.u, mz.v, bits(cv), 0).
+__device__ __forceinline__ void block_frame(const ViewGeo *vg, float bX, float bY, float bZ, float4 out[3]) {
+    const float4 *g4 = reinterpret_cast<const float4 *>(vg);
+    const float4 h0 = g4[0], h1 = g4[1], l0 = g4[2], l1 = g4[3], hw = g4[4], lw = g4[5];
+    const int4 sh = reinterpret_cast<const int4 *>(vg)[6];
+    // hu = (u0, v0, u1, v1 | u2, v2, u3, v3): columns x, y, z, translation
+    float su = h1.z, eu = l1.z, sv = h1.w, ev = l1.w, sw = hw.w, ew = lw.w;
+    df_add_term(h0.x, l0.x, bX, su, eu);
+    df_add_term(h0.z, l0.z, bY, su, eu);
+    df_add_term(h1.x, l1.x, bZ, su, eu);
+    df_add_term(h0.y, l0.y, bX, sv, ev);
+    df_add_term(h0.w, l0.w, bY, sv, ev);
+    df_add_term(h1.y, l1.y, bZ, sv, ev);
+    df_add_term(hw.x, lw.x, bX, sw, ew);
+    df_add_term(hw.y, lw.y, bY, sw, ew);
+    df_add_term(hw.z, lw.z, bZ, sw, ew);
+    const float wb = sw + ew;
+    const float rb = rcp_approx(wb);
+    const float cub = rintf((su + eu) * rb);                                // any nearby integer will do
+    const float cvb = rintf((sv + ev) * rb);
+    const float pu = cub * sw, pv = cvb * sw;
+    const float tu = (su - pu) + ((eu - fmaf(cub, sw, -pu)) - cub * ew);   // u'(corner) - cub w(corner)
+    const float tv = (sv - pv) + ((ev - fmaf(cvb, sw, -pv)) - cvb * ew);
+    // the shift scales with each voxel's own w: the local rows are (u' - cub w, v' - cvb w)
+    out[0] = make_float4(tu, tv, wb, __int_as_float(sh.x + static_cast<int>(cub)));
+    out[1] = make_float4(fmaf(-cub, hw.x, h0.x), fmaf(-cvb, hw.x, h0.y), fmaf(-cub, hw.y, h0.z), fmaf(-cvb, hw.y, h0.w));
+    out[2] = make_float4(fmaf(-cub, hw.z, h1.x), fmaf(-cvb, hw.z, h1.y), __int_as_float(sh.y + static_cast<int>(cvb)), 0.f);
+}
+
 template <int G, int DT, int XV, int R, int ROUTE>
 __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParams p) {
     const int L = p.L;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * XV;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z0 = blockIdx.z * R;
+    // the block's first voxel (centred coordinates, exact) and this thread's offset from it
+    const float bX = static_cast<float>(blockIdx.x * blockDim.x * XV) - p.cen;
+    const float bY = static_cast<float>(blockIdx.y * blockDim.y) - p.cen;
+    const float bZ = static_cast<float>(z0) - p.cen;
+    const float lx = static_cast<float>(threadIdx.x * XV);
+    const float ly = static_cast<float>(threadIdx.y);
+
+    // Block frames of the pass's views: lane k of the first warp evaluates view k once for the
+    // whole block (K <= 32); every thread reaches the barrier before any of them leaves.
+    __shared__ float4 s_frame[G == G_SOFT ? KMAX : 1][3];
+    if constexpr (G == G_SOFT) {
+        if (p.geo) {
+            const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+            if (tid < p.K) block_frame(p.geo + p.first_view + tid, bX, bY, bZ, s_frame[tid]);
+            __syncthreads();
+        }
+    }
     if (x0 >= L || y >= L) return;
     const size_t plane = static_cast<size_t>(L) * L;
     float *vb = p.vol + static_cast<size_t>(z0) * plane + static_cast<size_t>(y) * L + x0;
@@ -247,13 +289,6 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
 
     const float xc0 = static_cast<float>(x0) - p.cen;
     const float yc = static_cast<float>(y) - p.cen;
-    const float zc0 = static_cast<float>(z0) - p.cen;
-    // the block's first voxel (centred coordinates, exact) and this thread's offset from it
-    const float bX = static_cast<float>(blockIdx.x * blockDim.x * XV) - p.cen;
-    const float bY = static_cast<float>(blockIdx.y * blockDim.y) - p.cen;
-    const float bZ = zc0;
-    const float lx = static_cast<float>(threadIdx.x * XV);
-    const float ly = static_cast<float>(threadIdx.y);
     const int tex_zrun = p.tex_zrun;   // z positions [0, tex_zrun) use the texture route
 
 #pragma unroll 1
@@ -262,55 +297,35 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
         const float2 *muv = reinterpret_cast<const float2 *>(v.muv);
         const float *mw = v.mw;
         ViewConsts c;
-        c.m_z = muv[2];
         c.w_z = mw[2];
         c.tex = static_cast<cudaTextureObject_t>(v.tex);
         c.img = v.img;
         c.quad = v.quad;
-        float2 m_x = muv[0];
-        float2 buv;
+        float2 m_x, buv;
         float bw;
-        if constexpr (G == G_SOFT) {
-            // Block frame: (u', v', w) at the block's first voxel in double-float (uniform across the
-            // block), minus a block-local integer pixel shift; threads add short local offsets.
-            const float *hu = v.muv, *lu = v.muv_lo;
-            float su = hu[6], eu = lu[6], sv = hu[7], ev = lu[7], sw = mw[3], ew = v.mw_lo[3];
-            df_add_term(hu[0], lu[0], bX, su, eu);
-            df_add_term(hu[2], lu[2], bY, su, eu);
-            df_add_term(hu[4], lu[4], bZ, su, eu);
-            df_add_term(hu[1], lu[1], bX, sv, ev);
-            df_add_term(hu[3], lu[3], bY, sv, ev);
-            df_add_term(hu[5], lu[5], bZ, sv, ev);
-            df_add_term(mw[0], v.mw_lo[0], bX, sw, ew);
-            df_add_term(mw[1], v.mw_lo[1], bY, sw, ew);
-            df_add_term(mw[2], v.mw_lo[2], bZ, sw, ew);
-            const float wb = sw + ew;
-            const float rb = rcp_approx(wb);
-            const float cub = rintf((su + eu) * rb);                        // any nearby integer will do
-            const float cvb = rintf((sv + ev) * rb);
-            const float pu = cub * sw, pv = cvb * sw;
-            const float tu = (su - pu) + ((eu - fmaf(cub, sw, -pu)) - cub * ew);   // u'(corner) - cub * w(corner)
-            const float tv = (sv - pv) + ((ev - fmaf(cvb, sw, -pv)) - cvb * ew);
-            c.cu = v.cu + static_cast<int>(cub);
-            c.cv = v.cv + static_cast<int>(cvb);
-            c.gofs = make_float2(-(kMagic - static_cast<float>(c.cu + 1)), -(kMagic - static_cast<float>(c.cv + 1)));
-            c.qcx = kMagicBits - c.cu - 1;
-            c.qcy = kMagicBits - c.cv - 1;
-            // the shift scales with each voxel's own w: the local rows are (u' - cub w, v' - cvb w)
-            const float2 nshift = make_float2(-cub, -cvb);
-            m_x = __ffma2_rn(nshift, make_float2(mw[0], mw[0]), muv[0]);
-            const float2 m_y = __ffma2_rn(nshift, make_float2(mw[1], mw[1]), muv[1]);
-            c.m_z = __ffma2_rn(nshift, make_float2(mw[2], mw[2]), muv[2]);
-            buv = __ffma2_rn(make_float2(lx, lx), m_x, __ffma2_rn(make_float2(ly, ly), m_y, make_float2(tu, tv)));
-            bw = fmaf(mw[0], lx, fmaf(mw[1], ly, wb));
+        if (G == G_SOFT && p.geo) {
+            const float4 f0 = s_frame[k][0], f1 = s_frame[k][1], f2 = s_frame[k][2];
+            m_x = make_float2(f1.x, f1.y);
+            c.m_z = make_float2(f2.x, f2.y);
+            c.cu = __float_as_int(f0.w);
+            c.cv = __float_as_int(f2.z);
+            buv = __ffma2_rn(make_float2(lx, lx), m_x,
+                             __ffma2_rn(make_float2(ly, ly), make_float2(f1.z, f1.w), make_float2(f0.x, f0.y)));
+            bw = fmaf(mw[0], lx, fmaf(mw[1], ly, f0.z));
         } else {
-            // Texture-unit filtering needs absolute texture coordinates: the plain centred frame.
+            // Global frame (texture-unit filtering needs absolute texture coordinates, and the
+            // allocation-free entry point carries no geometry table).
+            m_x = muv[0];
+            c.m_z = muv[2];
             buv = __ffma2_rn(make_float2(xc0, xc0), muv[0],
-                             __ffma2_rn(make_float2(yc, yc), muv[1], __ffma2_rn(make_float2(zc0, zc0), muv[2], muv[3])));
-            bw = fmaf(mw[0], xc0, fmaf(mw[1], yc, fmaf(mw[2], zc0, mw[3])));
+                             __ffma2_rn(make_float2(yc, yc), muv[1], __ffma2_rn(make_float2(bZ, bZ), muv[2], muv[3])));
+            bw = fmaf(mw[0], xc0, fmaf(mw[1], yc, fmaf(mw[2], bZ, mw[3])));
             c.cu = v.cu;
             c.cv = v.cv;
         }
+        c.gofs = make_float2(-(kMagic - static_cast<float>(c.cu + 1)), -(kMagic - static_cast<float>(c.cv + 1)));
+        c.qcx = kMagicBits - c.cu - 1;
+        c.qcy = kMagicBits - c.cv - 1;
         if constexpr (G == G_SOFT) {
             // Clipping per run (the paper's clipping mask, Section "Implementation"): the
             // thread's voxels form a segment (XV = 1) or parallelogram in (x, z); its projection

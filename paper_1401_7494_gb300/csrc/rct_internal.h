@@ -27,29 +27,36 @@ enum DType : int { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 // centre projects -- keeps u' and v' small, so FP32 rounding of the
 // coordinates stays close to one rounding of the final pixel position.
 //
-// The matrix is split into FP32 high parts and the FP32 rounding of the remainders (low parts):
-// a block evaluates its corner's (u', v', w) once per view in double-float arithmetic from both,
-// picks a block-local integer shift, and its threads then work with small local coordinates, so the
-// FP32 pixel coordinate is accurate to a few units in the last place of a short local distance
-// wherever the block sits on the detector.
+// ViewGeo (device memory, one per view of the context, uploaded by rct_set_geometry) holds the
+// same matrix split into FP32 high parts and the FP32 rounding of the remainders (low parts).
+// With it, the first warp of a block evaluates the block corner's (u', v', w) for each view of
+// the pass in double-float arithmetic, picks a block-local integer shift, and the block's
+// threads then work with short local offsets, so the FP32 pixel coordinate is accurate to a
+// few units in the last place of a short local distance wherever the block sits on the detector.
 struct ViewParams {
-    float muv[8];              // rows u', v' interleaved, high parts: (m0, m4), (m1, m5), (m2, m6), (m3, m7)
-    float mw[4];               // row w, high parts
-    float muv_lo[8];           // low parts, same order
-    float mw_lo[4];
+    float muv[8];              // rows u', v' interleaved: (m0, m4), (m1, m5), (m2, m6), (m3, m7)
+    float mw[4];               // row w
     int cu, cv;                // integer detector shift of the fold (0 for texture-filtered sampling)
     unsigned long long tex;    // cudaTextureObject_t (gather or filtered texture)
     const void *img;           // linear image, H x W, row-major (plain loads)
     const void *quad;          // staged quad or pair image, zero padded (quad / pair loads)
 };
 
+struct __align__(16) ViewGeo {
+    float hu[8], lu[8];        // rows u', v' interleaved as in ViewParams: high and low parts
+    float hw[4], lw[4];        // row w: high and low parts
+    int cu, cv;
+    int pad_[2];
+};
+
 // A quad element at padded (row jy, column ix) holds the cell with corner (i0, j0) =
 // (ix - 1, jy - 1) in the order (I[j0][i0], I[j0+1][i0], I[j0][i0+1], I[j0+1][i0+1]), zero where
-// a tap lies off the image; FP32 quads are 16 bytes, FP16/BF16 quads 8 bytes.
-// A pair element at padded (row jy, column ix) holds the vertical pair (I[jy-1][ix-1], I[jy][ix-1]);
-// the image has H + 1 rows of W + 2 pairs, and the cell with corner (i0, j0) is the two
-// consecutive pairs at (j0 + 1, i0 + 1) and (j0 + 1, i0 + 2).  FP32 pairs are 8 bytes, FP16/BF16
-// pairs 4 bytes.
+// a tap lies off the image; the quad image has H + 2 rows of W + 2 elements (16 bytes FP32,
+// 8 bytes FP16/BF16).  A pair element at (row jy, column ix) holds the vertical pair
+// (I[jy-1][ix-1], I[jy][ix-1]); the pair image has H + 2 rows of W + 3 pairs (8 bytes FP32, 4 bytes
+// FP16/BF16), and the cell with corner (i0, j0) is the two consecutive pairs at (j0 + 1, i0 + 1).
+// In both layouts the last row and the last column(s) are all zero, so a kernel clamps an
+// unsigned cell index to them (any index off the image lands on zeros) instead of testing it.
 
 struct BpParams {
     float *vol;      // L^3, z-major, x fastest
@@ -59,6 +66,8 @@ struct BpParams {
     int accumulate;  // 0: the volume is logically zero, overwrite instead of adding
     int tex_zrun;    // G_SOFT: z positions [0, tex_zrun) of each run use the texture gather
     int quad;        // G_SOFT load route: 0 = linear image, 1 = staged quads, 2 = staged pairs
+    const ViewGeo *geo;  // G_SOFT: the context's per-view geometry for block frames (null: global frame)
+    int first_view;      // view index of view[0] in geo
     ViewParams view[KMAX];
 };
 
@@ -84,9 +93,10 @@ size_t quad_bytes(int W, int H, int dtype);
 cudaError_t launch_stage_pairs(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s);
 size_t pair_bytes(int W, int H, int dtype);
 
-// Fill the matrix and the index constants of a view from its FP64 fold (rows u', v', w over
-// centred voxel coordinates) and integer detector shift.
+// Fill the matrix of a view (FP32) from its FP64 fold (rows u', v', w over centred voxel
+// coordinates) and integer detector shift; and the high/low split used for block frames.
 void set_view_geometry(ViewParams *vp, const double fold[12], int cu, int cv);
+void set_view_geo(ViewGeo *vg, const double fold[12], int cu, int cv);
 
 // Record a message for rct_last_error() on the calling thread and return `code`.
 rct_status rct_internal_fail(rct_status code, const char *fmt, ...);
