@@ -398,16 +398,6 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
 
 template <int G, int DT, int XV, int R, int ROUTE>
 cudaError_t launch_one(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
-    // The kernel uses no shared memory: ask for the largest L1 share of the L1/shared array
-    // (the gathers live in L1), once per device.
-    static bool carveout_set[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !carveout_set[dev]) {
-        if (cudaFuncSetAttribute(bp_kernel<G, DT, XV, R, ROUTE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 static_cast<int>(cudaSharedmemCarveoutMaxL1)) != cudaSuccess)
-            (void)cudaGetLastError();   // a preference only: clear the error, launch anyway
-        carveout_set[dev] = true;
-    }
     const int gx = (p.L / XV + c.bx - 1) / c.bx;
     const dim3 grid(gx, (p.L + c.by - 1) / c.by, (p.L + R - 1) / R);
     bp_kernel<G, DT, XV, R, ROUTE><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
