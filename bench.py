@@ -32,12 +32,12 @@ import numpy as np  # noqa: E402
 METRIC = "GUPS (voxel updates/s) at 512^3 x 496, FP32 projections"
 UNIT = "GUPS"
 
-# DRAM bytes (read + write) of one accumulating backprojection pass (K = 16 views, L = 512) from an ncu
+# DRAM bytes (read + write) of one accumulating backprojection pass (L = 512, 1248x960 views) from an ncu
 # capture of that launch, keyed by the tuning it ran with; a changed kernel or tuning has no entry
-# (traffic reported as null).  Source: profiles/bp_kernel_*_L512_ncu_full.md.
+# (traffic reported as null).  Source: profiles/bp_kernel_pair_f32_L512_ncu_full.md.
 TRAFFIC: dict = {
-    '{"block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0, "views_per_pass": 16, "xvec": 1, "zrun": 8}':
-        690_587_904 + 482_652_672,
+    '{"block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0, "views_per_pass": 24, "xvec": 1, "zrun": 8}':
+        786_269_696 + 482_268_160,
 }
 
 
@@ -193,7 +193,7 @@ def oracle_rate(w, host_proj, target_s: float, max_planes: int | None = None):
 # ----------------------------------------------------------------------------- our arm
 
 def measure_variant(w, proj_dev, dtype: str, interp: str, steps: int, warmup: int, stream, check_idx=None,
-                    host=None):
+                    host=None, frame: str = "global"):
     """GUPS (and, when check_idx is given, error vs the oracle on sampled voxels) for one precision variant."""
     import torch
     from paper_1401_7494_gb300 import rct, tuning
@@ -205,9 +205,10 @@ def measure_variant(w, proj_dev, dtype: str, interp: str, steps: int, warmup: in
         data = torch.empty(proj_dev.shape, dtype=tdt, device=proj_dev.device)
         rct.rct_convert_projections(proj_dev, data, proj_dev.numel(), codes[dtype], stream)
     tun = tuning.lookup(w.L, dtype, interp)
-    out = {"tuning": tun}
+    out = {"tuning": tun, "frame": frame}
     with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
         bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_precision(codes[dtype], interp_code)
+        bp.set_frame(rct.RCT_FRAME_BLOCK if frame == "block" else rct.RCT_FRAME_GLOBAL)
         bp.set_tuning(**tun)
         for _ in range(warmup):
             bp.reset(stream)
@@ -363,9 +364,23 @@ def run_ours(args, dist: Dist) -> dict | None:
         wall = time.perf_counter() - t0
         e_ms = max(a0.elapsed_time(a1), wall * 1e3)
         e_ms = dist.max(e_ms)
+        # plain copy rates on this host link, to read the end-to-end number against
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        vol_dev = torch.empty((w.L,) * 3, dtype=torch.float32, device=dev)
+        c0.record(stream)
+        proj.copy_(pinned, non_blocking=True)
+        c1.record(stream)
+        vol_host.copy_(vol_dev, non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = pinned.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
+        d2h_gbs = vol_host.numel() * 4 / (c1.elapsed_time(c2) / 1e3) / 1e9
+        del vol_dev
         result["e2e"] = {"value": round(dist.sum(float(w.updates * e_steps)) / (e_ms / 1e3) / 1e9, 2), "unit": UNIT,
                          "h2d_bytes_per_step": int(pinned.numel() * 4), "d2h_bytes_per_step": int(vol_host.numel() * 4),
-                         "steps": e_steps, "api": "rct_backproject_host + rct_read_volume (pinned host buffers)"}
+                         "steps": e_steps, "api": "rct_backproject_host + rct_read_volume (pinned host buffers)",
+                         "ms_per_step": round(e_ms / e_steps, 3),
+                         "plain_copy_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)}}
         del pinned, vol_host
 
     bp.close()
@@ -377,10 +392,12 @@ def run_ours(args, dist: Dist) -> dict | None:
                                               np.arange(L * L, dtype=np.int64) + (L // 2) * L * L]))
         import oracle
         variants = {}
-        for dt, it in [("f32", "soft"), ("f16", "soft"), ("bf16", "soft"), ("f16", "tex"), ("f32", "tex")]:
+        for dt, it, fr in [("f32", "soft", "global"), ("f32", "soft", "block"), ("f16", "soft", "global"),
+                           ("bf16", "soft", "global"), ("f16", "tex", "global"), ("f32", "tex", "global")]:
             # the error is stated against the FP64 oracle on the FP32 projections
-            variants[f"{dt}_{it}"] = measure_variant(w, proj, dt, it, max(2, args.steps // 2), 1, stream,
-                                                     check_idx=check_idx, host=host)
+            name = f"{dt}_{it}" + ("_block_frame" if fr == "block" else "")
+            variants[name] = measure_variant(w, proj, dt, it, max(2, args.steps // 2), 1, stream,
+                                             check_idx=check_idx, host=host, frame=fr)
         result["variants"] = variants
         result["variants_note"] = ("GUPS per precision variant on the same workload; error vs the FP64 oracle on "
                                    f"FP32 projections over {check_idx.size} sampled voxels (a full z-plane + random)")

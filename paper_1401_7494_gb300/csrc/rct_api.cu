@@ -98,6 +98,7 @@ struct rct_ctx {
 
     int dtype = DT_F32;
     int interp = RCT_INTERP_SOFT;
+    int frame = RCT_FRAME_GLOBAL;
     rct_tuning tune{};              // gather may be RCT_GATHER_AUTO here
     bool tune_explicit_gather = false;
 
@@ -303,6 +304,7 @@ LaunchConfig launch_config(const rct_ctx *c, int kind) {
     lc.zrun = c->tune.zrun;
     lc.bx = c->tune.block_x;
     lc.by = c->tune.block_y;
+    lc.frame = (kind == G_SOFT && c->frame == RCT_FRAME_BLOCK) ? 1 : 0;
     return lc;
 }
 
@@ -315,7 +317,7 @@ void init_params(const rct_ctx *c, BpParams *p) {
     p->cen = 0.5f * (c->L - 1);
     p->tex_zrun = tex_zrun_of(c);
     p->quad = load_layout(c);
-    p->geo = c->geo_dev;
+    p->geo = (c->frame == RCT_FRAME_BLOCK) ? c->geo_dev : nullptr;
 }
 
 // FP32 view parameters for one view and kernel kind, from the FP64 fold.
@@ -566,8 +568,25 @@ rct_status rct_set_precision(rct_ctx *c, int proj_dtype, int interp) {
     if (!c) return fail(RCT_EINVAL, "null context");
     if (proj_dtype < RCT_PROJ_F32 || proj_dtype > RCT_PROJ_BF16) return fail(RCT_EINVAL, "unknown dtype %d", proj_dtype);
     if (interp != RCT_INTERP_SOFT && interp != RCT_INTERP_TEX) return fail(RCT_EINVAL, "unknown interp %d", interp);
+    if (c->frame == RCT_FRAME_BLOCK && (proj_dtype != RCT_PROJ_F32 || interp != RCT_INTERP_SOFT))
+        return fail(RCT_ENOTSUP, "block frames need FP32 projections and software interpolation");
     c->dtype = proj_dtype;
     c->interp = interp;
+    return RCT_OK;
+}
+
+rct_status rct_set_frame(rct_ctx *c, int frame) {
+    if (!c) return fail(RCT_EINVAL, "null context");
+    if (frame != RCT_FRAME_GLOBAL && frame != RCT_FRAME_BLOCK) return fail(RCT_EINVAL, "unknown frame %d", frame);
+    if (frame == RCT_FRAME_BLOCK && (c->dtype != DT_F32 || c->interp != RCT_INTERP_SOFT))
+        return fail(RCT_ENOTSUP, "block frames need FP32 projections and software interpolation");
+    c->frame = frame;
+    return RCT_OK;
+}
+
+rct_status rct_get_frame(const rct_ctx *c, int *frame) {
+    if (!c || !frame) return fail(RCT_EINVAL, "null pointer");
+    *frame = c->frame;
     return RCT_OK;
 }
 

@@ -12,22 +12,27 @@
 // divide, Section "SIMD Vectorization"); one packed multiply gives
 // q = (u' r, v' r).  floor(q) and frac(q) come from a packed add of
 // 1.5 * 2^23 rounded toward -inf (the integer part lands in the low mantissa
-// bits), so no conversion instruction is needed.
+// bits), so no conversion instruction is needed.  The coordinates are either
+// global (the folded matrix over centred voxel coordinates, its rows read from
+// kernel parameters into uniform registers) or block frames (FRAME: per block
+// and view, the block corner's coordinates in double-float and a block-local
+// integer shift, held in shared memory: smaller rounding error, more
+// registers per thread).
 //
-// Part 2 fetches the 2x2 cell by one of three routes (ROUTE below):
+// Part 2 fetches the 2x2 cell by one of these routes (ROUTE below):
 //   * texture gather (tld4) from a staged gather-capable array with a zero
 //     border -- the texture pipe;
 //   * one 128-bit (64-bit for 16-bit data) load of a staged "quad" element
 //     that holds the whole cell, from a zero-padded copy of the image (the
 //     paper's zero-padded projection buffer, Section "SIMD Vectorization",
 //     taken one step further) -- the load/store pipe;
+//   * two 64-bit (32-bit) loads of staged vertical pairs: the same cell in
+//     half the staged bytes, and neighbouring lanes share cache sectors;
 //   * four predicated loads straight from the caller's linear image (no
-//     staging at all).
-// The mixed route splits each z-run between the texture gather and the quad
-// load, so both fetch units work side by side (a 2x2 gather of 32-bit texels
-// costs the texture unit two slots).
+//     staging at all);
+//   * mixed: each z-run split between the texture gather and the quad load.
 // A view is skipped for a warp whose voxel runs all project off the detector.
-// Part 3: three lerps (two of them as one packed f32x2 pair for quads) and
+// Part 3: three lerps (two of them as one packed f32x2 pair) and
 // acc += val * r^2.
 #pragma once
 
@@ -92,11 +97,20 @@ struct ViewConsts {
 //   ROUTE_PLD: every z position by two loads of staged vertical pairs.
 enum Route : int { ROUTE_TEX = 0, ROUTE_LDG = 1, ROUTE_QLD = 2, ROUTE_MIX = 3, ROUTE_PLD = 4 };
 
+// Floor and fraction of q = uv * r (r = 1 / w): the packed add of 1.5 * 2^23 rounded toward -inf
+// gives t = kMagic + floor(q), whose low bits are floor(q) as an integer; f = q - floor(q) exactly.
+// (Folding the multiply into a directed-rounding FMA saves an instruction but measured slower:
+// the compiler's schedule of the z-run changes with it.)
+__device__ __forceinline__ void floor_frac(float2 uv, float rw, float2 &t, float2 &f) {
+    const float2 q = __fmul2_rn(uv, make_float2(rw, rw));
+    t = __fadd2_rd(q, make_float2(kMagic, kMagic));
+    f = __ffma2_rn(__fadd2_rn(t, make_float2(-kMagic, -kMagic)), make_float2(-1.0f, -1.0f), q);
+}
+
 // Part 2 + 3 by texture gather: adds the bilinear value at detector (cu + q.x, cv + q.y), times
 // w2, to acc.  Taps off the detector read the texture's zero border.
 template <int DT>
-__device__ __forceinline__ void accumulate_tex(const ViewConsts &c, float2 q, float w2, float &acc) {
-    const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));           // kMagic + floor(q)
+__device__ __forceinline__ void accumulate_tex(const ViewConsts &c, float2 t, float2 f, float w2, float &acc) {
     // The gather footprint of coordinate (i0 + 1, j0 + 1) is exactly texels i0..i0+1 x
     // j0..j0+1 (texel centres at +0.5), independent of the unit's coordinate rounding.
     const float2 g = __fadd2_rn(t, c.gofs);
@@ -111,22 +125,23 @@ __device__ __forceinline__ void accumulate_tex(const ViewConsts &c, float2 q, fl
         const float4 v = tex2Dgather<float4>(c.tex, g.x, g.y, 0);
         a = v.w; b = v.z; cc = v.x; d = v.y;
     }
-    const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));         // floor(q), exact
-    const float2 f = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), q);          // q - floor(q), exact
     const float t0 = fmaf(f.x, b - a, a);
     const float t1 = fmaf(f.x, d - cc, cc);
     acc = fmaf(fmaf(f.y, t1 - t0, t0), w2, acc);
 }
 
-// Part 2 + 3 by one load of the staged quad element (see ViewParams).  The unsigned cell index is
-// clamped to the image's all-zero last row / column: a cell with no tap on the image adds 0.
+// Part 2 + 3 by one load of the staged quad element (see ViewParams).  A cell with no tap on the
+// image has no element: such a lane loads element 0, which every off-image lane of the warp
+// shares (one cached sector), and adds it with weight 0.
 template <int DT>
-__device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 q, float w2, int W, int H,
+__device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 t, float2 f, float w2, int W, int H,
                                                 float &acc) {
-    const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));
-    const unsigned ix = min(static_cast<unsigned>(__float_as_int(t.x) - c.qcx), static_cast<unsigned>(W + 1));
-    const unsigned jy = min(static_cast<unsigned>(__float_as_int(t.y) - c.qcy), static_cast<unsigned>(H + 1));
-    const unsigned e = jy * static_cast<unsigned>(W + 2) + ix;
+    const int ix = __float_as_int(t.x) - c.qcx;                             // padded index (i0 + 1, j0 + 1)
+    const int jy = __float_as_int(t.y) - c.qcy;
+    const bool on = static_cast<unsigned>(ix) <= static_cast<unsigned>(W) &&
+                    static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
+    const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 1) + static_cast<unsigned>(ix) : 0u;
+    w2 = on ? w2 : 0.0f;
     float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
     if constexpr (DT == DT_F32) {
         const float4 v = __ldg(static_cast<const float4 *>(c.quad) + e);
@@ -142,22 +157,22 @@ __device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 q, f
             bd = make_float2(__uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
         }
     }
-    const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));         // floor(q), exact
-    const float2 f = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), q);          // q - floor(q), exact
     // both rows lerped along x at once: (t0, t1) = ac + f.x * (bd - ac)
     const float2 rows = __ffma2_rn(make_float2(f.x, f.x), __ffma2_rn(ac, make_float2(-1.0f, -1.0f), bd), ac);
     acc = fmaf(fmaf(f.y, rows.y - rows.x, rows.x), w2, acc);
 }
 
 // Part 2 + 3 by two loads of consecutive staged vertical pairs (see ViewParams): neighbouring
-// lanes share cache sectors, so less data moves from L2 than with quads.  Same clamp as quads.
+// lanes share cache sectors, so less data moves from L2 than with quads.  Same off-image rule.
 template <int DT>
-__device__ __forceinline__ void accumulate_pair(const ViewConsts &c, float2 q, float w2, int W, int H,
+__device__ __forceinline__ void accumulate_pair(const ViewConsts &c, float2 t, float2 f, float w2, int W, int H,
                                                 float &acc) {
-    const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));
-    const unsigned ix = min(static_cast<unsigned>(__float_as_int(t.x) - c.qcx), static_cast<unsigned>(W + 1));
-    const unsigned jy = min(static_cast<unsigned>(__float_as_int(t.y) - c.qcy), static_cast<unsigned>(H + 1));
-    const unsigned e = jy * static_cast<unsigned>(W + 3) + ix;
+    const int ix = __float_as_int(t.x) - c.qcx;                             // padded index (i0 + 1, j0 + 1)
+    const int jy = __float_as_int(t.y) - c.qcy;
+    const bool on = static_cast<unsigned>(ix) <= static_cast<unsigned>(W) &&
+                    static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
+    const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 2) + static_cast<unsigned>(ix) : 0u;
+    w2 = on ? w2 : 0.0f;
     float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
     if constexpr (DT == DT_F32) {
         const float2 *pp = static_cast<const float2 *>(c.quad) + e;
@@ -174,16 +189,13 @@ __device__ __forceinline__ void accumulate_pair(const ViewConsts &c, float2 q, f
             bd = make_float2(__uint_as_float(v1 << 16), __uint_as_float(v1 & 0xffff0000u));
         }
     }
-    const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));
-    const float2 f = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), q);
     const float2 rows = __ffma2_rn(make_float2(f.x, f.x), __ffma2_rn(ac, make_float2(-1.0f, -1.0f), bd), ac);
     acc = fmaf(fmaf(f.y, rows.y - rows.x, rows.x), w2, acc);
 }
 
 // Part 2 + 3 by four predicated loads from the caller's linear image (no staging).
 template <int DT>
-__device__ __forceinline__ void accumulate_ldg(const ViewConsts &c, float2 q, float w2, int W, int H, float &acc) {
-    const float2 t = __fadd2_rd(q, make_float2(kMagic, kMagic));
+__device__ __forceinline__ void accumulate_ldg(const ViewConsts &c, float2 t, float2 f, float w2, int W, int H, float &acc) {
     const int i0 = __float_as_int(t.x) - kMagicBits + c.cu;
     const int j0 = __float_as_int(t.y) - kMagicBits + c.cv;
     const bool x0 = static_cast<unsigned>(i0) < static_cast<unsigned>(W);
@@ -195,8 +207,6 @@ __device__ __forceinline__ void accumulate_ldg(const ViewConsts &c, float2 q, fl
     const float b = (y0 && x1) ? load_px<DT>(c.img, o + 1) : 0.0f;
     const float cc = (y1 && x0) ? load_px<DT>(c.img, o + W) : 0.0f;
     const float d = (y1 && x1) ? load_px<DT>(c.img, o + W + 1) : 0.0f;
-    const float2 fl = __fadd2_rn(t, make_float2(-kMagic, -kMagic));
-    const float2 f = __ffma2_rn(fl, make_float2(-1.0f, -1.0f), q);
     const float t0 = fmaf(f.x, b - a, a);
     const float t1 = fmaf(f.x, d - cc, cc);
     acc = fmaf(fmaf(f.y, t1 - t0, t0), w2, acc);
@@ -206,7 +216,7 @@ __device__ __forceinline__ void accumulate_ldg(const ViewConsts &c, float2 q, fl
 // image has it in [0, W] x [0, H].
 __device__ __forceinline__ int2 cell_index(const ViewConsts &c, float2 uv, float w) {
     const float rw = rcp_approx(w);
-    const float2 t = __fadd2_rd(__fmul2_rn(uv, make_float2(rw, rw)), make_float2(kMagic, kMagic));
+    const float2 t = __ffma2_rd(uv, make_float2(rw, rw), make_float2(kMagic, kMagic));   // kMagic + floor(uv r)
     return make_int2(__float_as_int(t.x) - c.qcx, __float_as_int(t.y) - c.qcy);
 }
 
@@ -241,8 +251,11 @@ __device__ __forceinline__ void block_frame(const ViewGeo *vg, float bX, float b
     out[2] = make_float4(fmaf(-cub, hw.z, h1.x), fmaf(-cvb, hw.z, h1.y), __int_as_float(sh.y + static_cast<int>(cvb)), 0.f);
 }
 
-template <int G, int DT, int XV, int R, int ROUTE>
+// FRAME: block frames (needs p.geo) instead of the global frame; the texture-filtered kernel
+// always takes the global frame (the texture unit needs absolute coordinates).
+template <int G, int DT, int XV, int R, int ROUTE, bool FRAME>
 __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParams p) {
+    static_assert(!FRAME || G == G_SOFT, "block frames are for the software gathers");
     const int L = p.L;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * XV;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -254,19 +267,26 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
     const float lx = static_cast<float>(threadIdx.x * XV);
     const float ly = static_cast<float>(threadIdx.y);
 
+    const bool inside = x0 < L && y < L;
+    const size_t plane = static_cast<size_t>(L) * L;
+    float *vb = p.vol + (inside ? static_cast<size_t>(z0) * plane + static_cast<size_t>(y) * L + x0 : 0);
+    // The volume rows of the run are requested into L2 first (without holding registers), so the
+    // DRAM latency overlaps the set-up below.
+    if (inside && p.accumulate) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (z0 + r < L) asm volatile("prefetch.global.L2 [%0];" :: "l"(vb + r * plane));
+    }
+
     // Block frames of the pass's views: lane k of the first warp evaluates view k once for the
     // whole block (K <= 32); every thread reaches the barrier before any of them leaves.
-    __shared__ float4 s_frame[G == G_SOFT ? KMAX : 1][3];
-    if constexpr (G == G_SOFT) {
-        if (p.geo) {
-            const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-            if (tid < p.K) block_frame(p.geo + p.first_view + tid, bX, bY, bZ, s_frame[tid]);
-            __syncthreads();
-        }
+    __shared__ float4 s_frame[FRAME ? KMAX : 1][3];
+    if constexpr (FRAME) {
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        if (tid < p.K) block_frame(p.geo + p.first_view + tid, bX, bY, bZ, s_frame[tid]);
+        __syncthreads();
     }
-    if (x0 >= L || y >= L) return;
-    const size_t plane = static_cast<size_t>(L) * L;
-    float *vb = p.vol + static_cast<size_t>(z0) * plane + static_cast<size_t>(y) * L + x0;
+    if (!inside) return;
 
     // The volume is touched once per pass: streaming (evict-first) loads and stores keep it from
     // displacing the projection data the gathers reuse in L1 and L2.
@@ -303,7 +323,7 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
         c.quad = v.quad;
         float2 m_x, buv;
         float bw;
-        if (G == G_SOFT && p.geo) {
+        if constexpr (FRAME) {
             const float4 f0 = s_frame[k][0], f1 = s_frame[k][1], f2 = s_frame[k][2];
             m_x = make_float2(f1.x, f1.y);
             c.m_z = make_float2(f2.x, f2.y);
@@ -313,8 +333,7 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
                              __ffma2_rn(make_float2(ly, ly), make_float2(f1.z, f1.w), make_float2(f0.x, f0.y)));
             bw = fmaf(mw[0], lx, fmaf(mw[1], ly, f0.z));
         } else {
-            // Global frame (texture-unit filtering needs absolute texture coordinates, and the
-            // allocation-free entry point carries no geometry table).
+            // Global frame: the matrix rows stay in kernel parameters, read into uniform registers.
             m_x = muv[0];
             c.m_z = muv[2];
             buv = __ffma2_rn(make_float2(xc0, xc0), muv[0],
@@ -361,23 +380,27 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
                 const float2 uv = (j == 0) ? uvr : __ffma2_rn(make_float2(fj, fj), m_x, uvr);
                 const float w = (j == 0) ? wr : fmaf(fj, mw[0], wr);
                 const float rw = rcp_approx(w);
-                const float2 q = __fmul2_rn(uv, make_float2(rw, rw));
                 const float w2 = rw * rw;
                 if constexpr (G == G_TEXLIN) {
                     // Texture-unit bilinear; the matrix already carries the +0.5 texel-centre shift.
+                    const float2 q = __fmul2_rn(uv, make_float2(rw, rw));
                     acc[r][j] = fmaf(tex2D<float>(c.tex, q.x, q.y), w2, acc[r][j]);
-                } else if constexpr (ROUTE == ROUTE_TEX) {
-                    accumulate_tex<DT>(c, q, w2, acc[r][j]);
-                } else if constexpr (ROUTE == ROUTE_LDG) {
-                    accumulate_ldg<DT>(c, q, w2, p.W, p.H, acc[r][j]);
-                } else if constexpr (ROUTE == ROUTE_QLD) {
-                    accumulate_quad<DT>(c, q, w2, p.W, p.H, acc[r][j]);
-                } else if constexpr (ROUTE == ROUTE_PLD) {
-                    accumulate_pair<DT>(c, q, w2, p.W, p.H, acc[r][j]);
-                } else if (r < tex_zrun) {
-                    accumulate_tex<DT>(c, q, w2, acc[r][j]);
                 } else {
-                    accumulate_quad<DT>(c, q, w2, p.W, p.H, acc[r][j]);
+                    float2 t, f;
+                    floor_frac(uv, rw, t, f);
+                    if constexpr (ROUTE == ROUTE_TEX) {
+                        accumulate_tex<DT>(c, t, f, w2, acc[r][j]);
+                    } else if constexpr (ROUTE == ROUTE_LDG) {
+                        accumulate_ldg<DT>(c, t, f, w2, p.W, p.H, acc[r][j]);
+                    } else if constexpr (ROUTE == ROUTE_QLD) {
+                        accumulate_quad<DT>(c, t, f, w2, p.W, p.H, acc[r][j]);
+                    } else if constexpr (ROUTE == ROUTE_PLD) {
+                        accumulate_pair<DT>(c, t, f, w2, p.W, p.H, acc[r][j]);
+                    } else if (r < tex_zrun) {
+                        accumulate_tex<DT>(c, t, f, w2, acc[r][j]);
+                    } else {
+                        accumulate_quad<DT>(c, t, f, w2, p.W, p.H, acc[r][j]);
+                    }
                 }
             }
         }
@@ -396,34 +419,38 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
     }
 }
 
-template <int G, int DT, int XV, int R, int ROUTE>
+template <int G, int DT, int XV, int R, int ROUTE, bool FRAME>
 cudaError_t launch_one(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
+    if (FRAME && !p.geo) return cudaErrorInvalidValue;
     const int gx = (p.L / XV + c.bx - 1) / c.bx;
     const dim3 grid(gx, (p.L + c.by - 1) / c.by, (p.L + R - 1) / R);
-    bp_kernel<G, DT, XV, R, ROUTE><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
+    bp_kernel<G, DT, XV, R, ROUTE, FRAME><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
     return cudaGetLastError();
 }
 
-template <int G, int DT, int XV, int ROUTE>
+template <int G, int DT, int XV, int ROUTE, bool FRAME>
 cudaError_t dispatch_r(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     switch (c.zrun) {
-        case 1: return launch_one<G, DT, XV, 1, ROUTE>(c, p, s);
-        case 2: return launch_one<G, DT, XV, 2, ROUTE>(c, p, s);
-        case 4: return launch_one<G, DT, XV, 4, ROUTE>(c, p, s);
-        case 8: return launch_one<G, DT, XV, 8, ROUTE>(c, p, s);
+        case 1: return launch_one<G, DT, XV, 1, ROUTE, FRAME>(c, p, s);
+        case 2: return launch_one<G, DT, XV, 2, ROUTE, FRAME>(c, p, s);
+        case 4: return launch_one<G, DT, XV, 4, ROUTE, FRAME>(c, p, s);
+        case 8: return launch_one<G, DT, XV, 8, ROUTE, FRAME>(c, p, s);
         case 16:
-            if constexpr (XV <= 2) return launch_one<G, DT, XV, 16, ROUTE>(c, p, s);
+            if constexpr (XV <= 2) return launch_one<G, DT, XV, 16, ROUTE, FRAME>(c, p, s);
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }
 
+// Block frames are compiled for the FP32 software gathers only (the API rejects them elsewhere).
 template <int G, int DT, int ROUTE>
 cudaError_t dispatch_xv(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
+    constexpr bool kFrames = (G == G_SOFT && DT == DT_F32);
+    if (c.frame && !kFrames) return cudaErrorInvalidValue;
     switch (c.xv) {
-        case 1: return dispatch_r<G, DT, 1, ROUTE>(c, p, s);
-        case 2: return dispatch_r<G, DT, 2, ROUTE>(c, p, s);
-        case 4: return dispatch_r<G, DT, 4, ROUTE>(c, p, s);
+        case 1: return c.frame ? dispatch_r<G, DT, 1, ROUTE, kFrames>(c, p, s) : dispatch_r<G, DT, 1, ROUTE, false>(c, p, s);
+        case 2: return c.frame ? dispatch_r<G, DT, 2, ROUTE, kFrames>(c, p, s) : dispatch_r<G, DT, 2, ROUTE, false>(c, p, s);
+        case 4: return c.frame ? dispatch_r<G, DT, 4, ROUTE, kFrames>(c, p, s) : dispatch_r<G, DT, 4, ROUTE, false>(c, p, s);
         default: return cudaErrorInvalidValue;
     }
 }

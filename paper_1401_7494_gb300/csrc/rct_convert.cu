@@ -86,14 +86,13 @@ __device__ __forceinline__ T px_or_zero(const T *img, int W, int H, int i, int j
                ? img[static_cast<size_t>(j) * W + i] : T(0);
 }
 
-// One thread per padded element (jy, ix) of the (H + 2) x (W + 2) quad image: the 2x2 cell with
-// corner (ix - 1, jy - 1); the last row and column hold only off-image taps, i.e. zeros.
+// One thread per padded element (jy, ix): gathers the 2x2 cell with corner (ix - 1, jy - 1).
 __global__ void stage_quads_f32(const float *__restrict__ img, float4 *__restrict__ q, int W, int H) {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int jy = blockIdx.y;
-    if (ix > W + 1) return;
+    if (ix > W) return;
     const int i0 = ix - 1, j0 = jy - 1;
-    q[static_cast<size_t>(jy) * (W + 2) + ix] =
+    q[static_cast<size_t>(jy) * (W + 1) + ix] =
         make_float4(px_or_zero(img, W, H, i0, j0), px_or_zero(img, W, H, i0, j0 + 1),
                     px_or_zero(img, W, H, i0 + 1, j0), px_or_zero(img, W, H, i0 + 1, j0 + 1));
 }
@@ -101,39 +100,38 @@ __global__ void stage_quads_f32(const float *__restrict__ img, float4 *__restric
 __global__ void stage_quads_u16(const unsigned short *__restrict__ img, uint2 *__restrict__ q, int W, int H) {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int jy = blockIdx.y;
-    if (ix > W + 1) return;
+    if (ix > W) return;
     const int i0 = ix - 1, j0 = jy - 1;
     const unsigned a = px_or_zero(img, W, H, i0, j0), c = px_or_zero(img, W, H, i0, j0 + 1);
     const unsigned b = px_or_zero(img, W, H, i0 + 1, j0), d = px_or_zero(img, W, H, i0 + 1, j0 + 1);
-    q[static_cast<size_t>(jy) * (W + 2) + ix] = make_uint2(a | (c << 16), b | (d << 16));
+    q[static_cast<size_t>(jy) * (W + 1) + ix] = make_uint2(a | (c << 16), b | (d << 16));
 }
 
-// One thread per padded pair (jy, ix) of the (H + 2) x (W + 3) pair image:
-// (I[jy-1][ix-1], I[jy][ix-1]), zero off the image.
+// One thread per padded pair (jy, ix): (I[jy-1][ix-1], I[jy][ix-1]), zero off the image.
 __global__ void stage_pairs_f32(const float *__restrict__ img, float2 *__restrict__ q, int W, int H) {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int jy = blockIdx.y;
-    if (ix > W + 2) return;
-    q[static_cast<size_t>(jy) * (W + 3) + ix] =
+    if (ix > W + 1) return;
+    q[static_cast<size_t>(jy) * (W + 2) + ix] =
         make_float2(px_or_zero(img, W, H, ix - 1, jy - 1), px_or_zero(img, W, H, ix - 1, jy));
 }
 
 __global__ void stage_pairs_u16(const unsigned short *__restrict__ img, unsigned *__restrict__ q, int W, int H) {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int jy = blockIdx.y;
-    if (ix > W + 2) return;
+    if (ix > W + 1) return;
     const unsigned a = px_or_zero(img, W, H, ix - 1, jy - 1), c = px_or_zero(img, W, H, ix - 1, jy);
-    q[static_cast<size_t>(jy) * (W + 3) + ix] = a | (c << 16);
+    q[static_cast<size_t>(jy) * (W + 2) + ix] = a | (c << 16);
 }
 
 }  // namespace
 
 size_t pair_bytes(int W, int H, int dtype) {
-    return static_cast<size_t>(W + 3) * (H + 2) * (dtype == DT_F32 ? 8 : 4);
+    return static_cast<size_t>(W + 2) * (H + 1) * (dtype == DT_F32 ? 8 : 4);
 }
 
 cudaError_t launch_stage_pairs(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s) {
-    const dim3 block(256), grid((W + 3 + 255) / 256, H + 2);
+    const dim3 block(256), grid((W + 2 + 255) / 256, H + 1);
     if (dtype == DT_F32)
         stage_pairs_f32<<<grid, block, 0, s>>>(static_cast<const float *>(src), static_cast<float2 *>(dst), W, H);
     else
@@ -142,11 +140,11 @@ cudaError_t launch_stage_pairs(const void *src, void *dst, int W, int H, int dty
 }
 
 size_t quad_bytes(int W, int H, int dtype) {
-    return static_cast<size_t>(W + 2) * (H + 2) * (dtype == DT_F32 ? 16 : 8);
+    return static_cast<size_t>(W + 1) * (H + 1) * (dtype == DT_F32 ? 16 : 8);
 }
 
 cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s) {
-    const dim3 block(256), grid((W + 2 + 255) / 256, H + 2);
+    const dim3 block(256), grid((W + 1 + 255) / 256, H + 1);
     if (dtype == DT_F32)
         stage_quads_f32<<<grid, block, 0, s>>>(static_cast<const float *>(src), static_cast<float4 *>(dst), W, H);
     else

@@ -51,12 +51,12 @@ struct __align__(16) ViewGeo {
 
 // A quad element at padded (row jy, column ix) holds the cell with corner (i0, j0) =
 // (ix - 1, jy - 1) in the order (I[j0][i0], I[j0+1][i0], I[j0][i0+1], I[j0+1][i0+1]), zero where
-// a tap lies off the image; the quad image has H + 2 rows of W + 2 elements (16 bytes FP32,
-// 8 bytes FP16/BF16).  A pair element at (row jy, column ix) holds the vertical pair
-// (I[jy-1][ix-1], I[jy][ix-1]); the pair image has H + 2 rows of W + 3 pairs (8 bytes FP32, 4 bytes
-// FP16/BF16), and the cell with corner (i0, j0) is the two consecutive pairs at (j0 + 1, i0 + 1).
-// In both layouts the last row and the last column(s) are all zero, so a kernel clamps an
-// unsigned cell index to them (any index off the image lands on zeros) instead of testing it.
+// a tap lies off the image; the quad image has H + 1 rows of W + 1 elements (16 bytes FP32,
+// 8 bytes FP16/BF16).  A pair element at padded (row jy, column ix) holds the vertical pair
+// (I[jy-1][ix-1], I[jy][ix-1]); the pair image has H + 1 rows of W + 2 pairs (8 bytes FP32,
+// 4 bytes FP16/BF16), and the cell with corner (i0, j0) is the two consecutive pairs at
+// (j0 + 1, i0 + 1) and (j0 + 1, i0 + 2).  A cell with a tap on the image has its padded index in
+// [0, W] x [0, H]; a kernel tests that and sends every other lane to element 0.
 
 struct BpParams {
     float *vol;      // L^3, z-major, x fastest
@@ -77,6 +77,7 @@ struct LaunchConfig {
     int xv;      // voxels per thread along x: 1, 2, 4
     int zrun;    // voxels per thread along z: 1, 2, 4, 8
     int bx, by;  // block shape
+    int frame;   // 1: block frames (FP32 software gathers only; BpParams::geo set)
 };
 
 // Kernel launchers (one translation unit per gather kind).

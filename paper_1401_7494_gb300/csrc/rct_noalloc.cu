@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "../../include/rct.h"
+#include "rct_bp_kernel.cuh"
 #include "rct_internal.h"
 
 namespace {
@@ -128,7 +129,8 @@ extern "C" rct_status rct_backproject_f16_noalloc(int L, int det_w, int det_h, c
             vp.tex = 0;
             vp.img = scratch + static_cast<size_t>(k) * px;
         }
-        e = launch_bp_soft_f16(lc, p, s);
+        // global frame: this entry point keeps no per-view geometry table on the device
+        e = launch_one<G_SOFT, DT_F16, 1, 4, ROUTE_LDG, false>(lc, p, s);
         if (e != cudaSuccess) return rct_internal_fail(RCT_ECUDA, "backprojection launch: %s", cudaGetErrorString(e));
     }
     return RCT_OK;

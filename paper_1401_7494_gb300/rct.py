@@ -20,6 +20,7 @@ from . import build as _build
 RCT_OK, RCT_EINVAL, RCT_ENOMEM, RCT_ECUDA, RCT_ESTATE, RCT_ETIMEOUT, RCT_ENOTSUP = range(7)
 RCT_PROJ_F32, RCT_PROJ_F16, RCT_PROJ_BF16 = 0, 1, 2
 RCT_INTERP_SOFT, RCT_INTERP_TEX = 0, 1
+RCT_FRAME_GLOBAL, RCT_FRAME_BLOCK = 0, 1
 RCT_GATHER_AUTO, RCT_GATHER_LDG, RCT_GATHER_TLD4, RCT_GATHER_MIX, RCT_GATHER_QUAD, RCT_GATHER_PAIR = 0, 1, 2, 3, 4, 5
 RCT_MAX_VIEWS_PER_PASS = 32
 STATUS_NAMES = {0: "RCT_OK", 1: "RCT_EINVAL", 2: "RCT_ENOMEM", 3: "RCT_ECUDA", 4: "RCT_ESTATE",
@@ -52,6 +53,8 @@ SIGNATURES = {
     "rct_destroy": (None, [_P]),
     "rct_set_geometry": (_I, [_P, _D3, _D3, _D3]),
     "rct_set_precision": (_I, [_P, _I, _I]),
+    "rct_set_frame": (_I, [_P, _I]),
+    "rct_get_frame": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "rct_set_tuning": (_I, [_P, ctypes.POINTER(rct_tuning)]),
     "rct_get_tuning": (_I, [_P, ctypes.POINTER(rct_tuning)]),
     "rct_reset_volume": (_I, [_P, _P]),
@@ -169,6 +172,16 @@ def rct_set_geometry(ctx, matrices, origin, spacing) -> None:
 
 def rct_set_precision(ctx, proj_dtype: int, interp: int = RCT_INTERP_SOFT) -> None:
     _check(lib().rct_set_precision(ctx, int(proj_dtype), int(interp)))
+
+
+def rct_set_frame(ctx, frame: int) -> None:
+    _check(lib().rct_set_frame(ctx, int(frame)))
+
+
+def rct_get_frame(ctx) -> int:
+    f = ctypes.c_int()
+    _check(lib().rct_get_frame(ctx, ctypes.byref(f)))
+    return f.value
 
 
 def rct_set_tuning(ctx, views_per_pass=0, zrun=0, xvec=0, block_x=0, block_y=0, gather=0, tex_zrun=0) -> None:
@@ -335,6 +348,10 @@ class Backprojector:
 
     def set_precision(self, proj_dtype=RCT_PROJ_F32, interp=RCT_INTERP_SOFT):
         rct_set_precision(self.ctx, proj_dtype, interp)
+        return self
+
+    def set_frame(self, frame=RCT_FRAME_GLOBAL):
+        rct_set_frame(self.ctx, frame)
         return self
 
     def set_tuning(self, **kw):

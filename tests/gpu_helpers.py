@@ -52,13 +52,14 @@ def oracle_inputs(proj_f32_host: np.ndarray, dtype: str) -> np.ndarray:
 
 
 def gpu_backproject(w: synth.Workload, proj_dev: torch.Tensor, *, dtype="f32", interp=rct.RCT_INTERP_SOFT,
-                    tuning=None, first=0, n=None, chunks=None) -> np.ndarray:
+                    tuning=None, first=0, n=None, chunks=None, frame=rct.RCT_FRAME_GLOBAL) -> np.ndarray:
     """Backproject through the C ABI; returns the volume as (L, L, L) float32 numpy."""
     n = w.n_views if n is None else n
     stream = torch.cuda.current_stream()
     with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
         bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
         bp.set_precision(DTYPES[dtype][0], interp)
+        bp.set_frame(frame)
         if tuning:
             bp.set_tuning(**tuning)
         data = stored(proj_dev, dtype)

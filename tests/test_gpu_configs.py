@@ -37,9 +37,10 @@ def test_full_parity_L128_496_views(cuda_device):
     assert_parity(got, ref, "L=128 x 496 full volume")
 
 
-@pytest.mark.parametrize("name,dtype", [("fp32_L512", "f32"), ("fp32_L1024", "f32"), ("prec_L512", "f16"),
-                                        ("prec_L512", "bf16")])
-def test_sampled_parity_large(cuda_device, name, dtype):
+@pytest.mark.parametrize("name,dtype,frame", [("fp32_L512", "f32", "global"), ("fp32_L512", "f32", "block"),
+                                              ("fp32_L1024", "f32", "global"), ("prec_L512", "f16", "global"),
+                                              ("prec_L512", "bf16", "global")])
+def test_sampled_parity_large(cuda_device, name, dtype, frame):
     w = synth.workloads.named(name)
     proj = w.projections(device=cuda_device)
     host = proj.cpu().numpy()
@@ -48,6 +49,7 @@ def test_sampled_parity_large(cuda_device, name, dtype):
     with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
         bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
         bp.set_precision(DTYPES[dtype][0], rct.RCT_INTERP_SOFT)
+        bp.set_frame(rct.RCT_FRAME_BLOCK if frame == "block" else rct.RCT_FRAME_GLOBAL)
         bp.set_tuning(**tun)
         data = stored(proj, dtype)
         del proj
@@ -60,7 +62,9 @@ def test_sampled_parity_large(cuda_device, name, dtype):
     got = vol.view(-1)[torch.from_numpy(idx).to(cuda_device)].cpu().numpy()
     del vol
     ref = _sampled_reference(w, oracle_inputs(host, dtype), idx)
-    assert_parity(got, ref, f"{name} {dtype} sampled ({idx.size} voxels)")
+    # block frames keep every FP32 coordinate a short local offset: a ten times tighter bar
+    tol = 1e-6 if frame == "block" else 1e-5
+    assert_parity(got, ref, f"{name} {dtype} {frame} frame sampled ({idx.size} voxels)", rms_tol=tol)
 
 
 def test_maximum_volume_L2048(cuda_device):
@@ -99,4 +103,8 @@ def test_large_detector(cuda_device):
     tol = scaled_rms_tol(w.geom.det_w, w.n_views)
     for g in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_PAIR, rct.RCT_GATHER_QUAD, rct.RCT_GATHER_LDG):
         got = gpu_backproject(w, proj, tuning=dict(gather=g, views_per_pass=4))
-        assert_parity(got, ref, f"4096x3072 detector, gather {g}", rms_tol=tol)
+        rms_g, _ = assert_parity(got, ref, f"4096x3072 detector, gather {g}", rms_tol=tol)
+        # Block frames: here one voxel spans about 85 pixels, so a thread block's local offsets are
+        # as long as the global ones and the frame brings nothing; the same scaled bar.
+        got = gpu_backproject(w, proj, tuning=dict(gather=g, views_per_pass=4), frame=rct.RCT_FRAME_BLOCK)
+        assert_parity(got, ref, f"4096x3072 detector, gather {g}, block frame", rms_tol=tol)

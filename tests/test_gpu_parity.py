@@ -222,3 +222,50 @@ def test_all_gather_routes_agree_closely(small_cases):
     for g, v in vols.items():
         rms, mx = rel_errors(v, ref)
         assert rms < 1e-6 and mx < 1e-5, (g, rms, mx)
+
+
+# Block frames (rct_set_frame): the same parity bar on the small cases (their volumes span only a
+# few thread blocks, so the frame's gain shows at L = 512, tested with the sampled configurations).
+@pytest.mark.parametrize("case", sorted(SMALL))
+@pytest.mark.parametrize("ti", [1, 3, 4, 5, 7, 8, 9, 11, 12])
+def test_block_frame_parity_small(small_cases, case, ti):
+    w, proj, host = small_cases[case]
+    tuning = dict(TUNINGS[ti])
+    if w.L % tuning.get("xvec", 1):
+        tuning["xvec"] = 1
+    got = gpu_backproject(w, proj, tuning=tuning, frame=rct.RCT_FRAME_BLOCK)
+    assert_parity(got, oracle_volume(w, host), f"{case} block frame, tuning {tuning}")
+
+
+def test_block_frame_routes_agree(small_cases):
+    """With block frames too, every gather route fetches the same taps."""
+    w, proj, _ = small_cases["L64"]
+    vols = {g: gpu_backproject(w, proj, tuning=dict(gather=g, zrun=4, xvec=1, views_per_pass=16),
+                               frame=rct.RCT_FRAME_BLOCK)
+            for g in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG, rct.RCT_GATHER_QUAD, rct.RCT_GATHER_PAIR)}
+    ref = vols[rct.RCT_GATHER_LDG].astype(np.float64)
+    for g, v in vols.items():
+        rms, mx = rel_errors(v, ref)
+        assert rms < 1e-6 and mx < 1e-5, (g, rms, mx)
+
+
+def test_frame_argument_errors(cuda_device):
+    with rct.Backprojector(8, 16, 12, 4) as bp:
+        assert rct.rct_get_frame(bp.ctx) == rct.RCT_FRAME_GLOBAL
+        for bad in (-1, 2):
+            with pytest.raises(rct.RctError) as e:
+                bp.set_frame(bad)
+            assert e.value.status == rct.RCT_EINVAL
+        bp.set_frame(rct.RCT_FRAME_BLOCK)
+        assert rct.rct_get_frame(bp.ctx) == rct.RCT_FRAME_BLOCK
+        for dtype, interp in ((rct.RCT_PROJ_F16, rct.RCT_INTERP_SOFT), (rct.RCT_PROJ_BF16, rct.RCT_INTERP_SOFT),
+                              (rct.RCT_PROJ_F32, rct.RCT_INTERP_TEX)):
+            with pytest.raises(rct.RctError) as e:
+                bp.set_precision(dtype, interp)
+            assert e.value.status == rct.RCT_ENOTSUP
+        bp.set_frame(rct.RCT_FRAME_GLOBAL)
+        bp.set_precision(rct.RCT_PROJ_F16, rct.RCT_INTERP_SOFT)
+        with pytest.raises(rct.RctError) as e:
+            bp.set_frame(rct.RCT_FRAME_BLOCK)
+        assert e.value.status == rct.RCT_ENOTSUP
+        assert rct.rct_get_frame(bp.ctx) == rct.RCT_FRAME_GLOBAL
