@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--no-k-sweep", action="store_true", help="skip the views-per-pass sweep at L=1024")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--out", default=None, help="also write the JSON line to this file")
@@ -193,7 +194,7 @@ def oracle_rate(w, host_proj, target_s: float, max_planes: int | None = None):
 # ----------------------------------------------------------------------------- our arm
 
 def measure_variant(w, proj_dev, dtype: str, interp: str, steps: int, warmup: int, stream, check_idx=None,
-                    host=None, frame: str = "global"):
+                    host=None, frame: str = "global", trunc: bool = False):
     """GUPS (and, when check_idx is given, error vs the oracle on sampled voxels) for one precision variant."""
     import torch
     from paper_1401_7494_gb300 import rct, tuning
@@ -205,10 +206,11 @@ def measure_variant(w, proj_dev, dtype: str, interp: str, steps: int, warmup: in
         data = torch.empty(proj_dev.shape, dtype=tdt, device=proj_dev.device)
         rct.rct_convert_projections(proj_dev, data, proj_dev.numel(), codes[dtype], stream)
     tun = tuning.lookup(w.L, dtype, interp)
-    out = {"tuning": tun, "frame": frame}
+    out = {"tuning": tun, "frame": frame, "index_rule": "trunc" if trunc else "floor"}
     with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
         bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_precision(codes[dtype], interp_code)
         bp.set_frame(rct.RCT_FRAME_BLOCK if frame == "block" else rct.RCT_FRAME_GLOBAL)
+        bp.set_index_rule(rct.RCT_INDEX_TRUNC if trunc else rct.RCT_INDEX_FLOOR)
         bp.set_tuning(**tun)
         for _ in range(warmup):
             bp.reset(stream)
@@ -231,11 +233,51 @@ def measure_variant(w, proj_dev, dtype: str, interp: str, steps: int, warmup: in
             torch.cuda.synchronize()
             got = vol.view(-1)[torch.from_numpy(check_idx).to(vol.device)].cpu().numpy().astype(np.float64)
             ref = oracle.backproject_voxels(w.L, w.geom.det_w, w.geom.det_h, w.geom.matrices, w.origin, w.spacing,
-                                            host, check_idx, n_threads=oracle.max_threads())
+                                            host, check_idx, n_threads=oracle.max_threads(),
+                                            index_rule=oracle.INDEX_TRUNC if trunc else oracle.INDEX_FLOOR)
             out["rel_rms_vs_fp64_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
             out["max_abs_vs_fp64_oracle"] = float(np.abs(got - ref).max() / np.abs(ref).max())
     del data
     return out
+
+
+def k_sweep(dev, stream, peaks: dict) -> dict:
+    """Views per pass K against the volume stream at L = 1024 x 496: the volume is read and written once per
+    pass (8/K bytes of HBM per voxel update), so small K is HBM-bound and large K fetch-bound."""
+    import torch
+    import synth
+    from paper_1401_7494_gb300 import rct, tuning
+    w = synth.workloads.named("fp32_L1024")
+    proj = w.projections(device=dev)
+    base = tuning.lookup(w.L, "f32", "soft")
+    rows = []
+    vol_bytes = 4 * w.L ** 3
+    img_bytes = 4 * w.geom.det_w * w.geom.det_h
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
+        for K in (1, 4, 8, 16, 24, 32):
+            bp.set_tuning(**dict(base, views_per_pass=K))
+            bp.reset(stream)
+            bp.backproject(proj, 0, w.n_views, stream)
+            torch.cuda.synchronize()
+            steps = 1 if K == 1 else 2
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                bp.reset(stream)
+                bp.backproject(proj, 0, w.n_views, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3 / steps
+            passes = -(-w.n_views // K)
+            hbm_bytes = vol_bytes * (1 + 2 * (passes - 1)) + img_bytes * w.n_views
+            rows.append({"K": K, "gups": round(w.updates / sec / 1e9, 1), "s_per_step": round(sec, 4),
+                         "hbm_gbs": round(hbm_bytes / sec / 1e9, 1), "hbm_frac": round(hbm_bytes / sec / 1e9 / hbm_peak, 3)})
+    del proj
+    return {"workload": "fp32_L1024: 1024^3 x 496 views of 1248x960", "tuning": base, "rows": rows,
+            "note": "algorithmic HBM bytes per step: volume written by the first pass, read and written by the others, "
+                    "each view read once"}
 
 
 def run_ours(args, dist: Dist) -> dict | None:
@@ -392,18 +434,23 @@ def run_ours(args, dist: Dist) -> dict | None:
                                               np.arange(L * L, dtype=np.int64) + (L // 2) * L * L]))
         import oracle
         variants = {}
-        for dt, it, fr in [("f32", "soft", "global"), ("f32", "soft", "block"), ("f16", "soft", "global"),
-                           ("bf16", "soft", "global"), ("f16", "tex", "global"), ("f32", "tex", "global")]:
-            # the error is stated against the FP64 oracle on the FP32 projections
-            name = f"{dt}_{it}" + ("_block_frame" if fr == "block" else "")
+        for dt, it, fr, tr in [("f32", "soft", "global", False), ("f32", "soft", "block", False),
+                               ("f32", "soft", "global", True), ("f16", "soft", "global", False),
+                               ("bf16", "soft", "global", False), ("f16", "tex", "global", False),
+                               ("f32", "tex", "global", False)]:
+            # the error is stated against the FP64 oracle on the FP32 projections (with the same index rule)
+            name = f"{dt}_{it}" + ("_block_frame" if fr == "block" else "") + ("_rabbitct_trunc" if tr else "")
             variants[name] = measure_variant(w, proj, dt, it, max(2, args.steps // 2), 1, stream,
-                                             check_idx=check_idx, host=host, frame=fr)
+                                             check_idx=check_idx, host=host, frame=fr, trunc=tr)
         result["variants"] = variants
         result["variants_note"] = ("GUPS per precision variant on the same workload; error vs the FP64 oracle on "
                                    f"FP32 projections over {check_idx.size} sampled voxels (a full z-plane + random)")
 
     del proj
     torch.cuda.empty_cache()
+    if dist.rank == 0 and not args.no_k_sweep:
+        result["k_sweep"] = k_sweep(dev, stream, peaks)
+        torch.cuda.empty_cache()
     if dist.rank == 0 and not args.no_serve:
         from paper_1401_7494_gb300 import serve_bench
         protocols, host_data = serve_bench.build_protocols(dev)

@@ -90,6 +90,18 @@ typedef enum rct_frame {
                              L = 512), at a cost in speed (more registers per thread). */
 } rct_frame;
 
+/*
+ * How the cell of a detector coordinate ix is chosen.  Listing 1 (Section "Algorithm") casts with
+ * (int), which truncates toward zero: for ix in (-2, 0) that picks the cell one pixel to the right
+ * of floor's and gives the tap at ix's right a negative weight (the listing extrapolates from the
+ * image edge).  Floor treats the image as zero-extended and keeps the interpolant continuous; it is
+ * the reading this library uses by default.  The two agree wherever ix >= 0 and iy >= 0.
+ */
+typedef enum rct_index_rule {
+    RCT_INDEX_FLOOR = 0,  /* i0 = floor(ix) (default) */
+    RCT_INDEX_TRUNC = 1   /* i0 = (int) ix as in Listing 1: RabbitCT compatibility */
+} rct_index_rule;
+
 /* How a software-interpolated kernel fetches its four taps (Part 2). */
 typedef enum rct_gather {
     RCT_GATHER_AUTO = 0,  /* let the library (or the tuning cache) choose */
@@ -155,6 +167,26 @@ RCT_API rct_status rct_set_precision(rct_ctx *ctx, int proj_dtype, int interp);
  */
 RCT_API rct_status rct_set_frame(rct_ctx *ctx, int frame);
 RCT_API rct_status rct_get_frame(const rct_ctx *ctx, int *frame);
+
+/*
+ * RabbitCT compatibility (Listing 1's conventions, for data prepared for the RabbitCT framework).
+ *
+ * rct_set_index_rule chooses the cell rule (rct_index_rule; default RCT_INDEX_FLOOR).
+ * RCT_INDEX_TRUNC needs FP32 projections, software interpolation and the global frame
+ * (RCT_ENOTSUP otherwise, here and from a later rct_set_precision / rct_set_frame that would break
+ * that); it reads the caller's images with plain loads, whatever gather route the tuning names.
+ * The bounds test stays "column in [0, W), row in [0, H)" (the listing's test swaps width and
+ * height in print; its row stride is the width).
+ *
+ * rct_set_geometry_rabbitct takes the geometry as the RabbitCT module receives it: n_views 3x4
+ * FP32 matrices stored column-major (element (r, c) at A[3c + r], as Listing 1 reads A[0], A[3],
+ * A[6], A[9] for u), and the scalar origin O and voxel size MM (mm) shared by the three axes
+ * (world position of voxel (x, y, z) = (O + x MM, O + y MM, O + z MM)).  It widens them to FP64
+ * and calls rct_set_geometry, with the same errors.
+ */
+RCT_API rct_status rct_set_index_rule(rct_ctx *ctx, int rule);
+RCT_API rct_status rct_get_index_rule(const rct_ctx *ctx, int *rule);
+RCT_API rct_status rct_set_geometry_rabbitct(rct_ctx *ctx, const float *matrices, float O, float MM);
 
 /* Override the kernel tuning (see rct_tuning).  Validated synchronously. */
 RCT_API rct_status rct_set_tuning(rct_ctx *ctx, const rct_tuning *t);

@@ -10,7 +10,7 @@ Listing 1 (Section "Algorithm") with the readings stated in its header; this
 module compiles it with gcc and exposes it through ctypes with numpy arrays.
 """
 from .oracle import (build, load, backproject, backproject_voxels, round_f16, round_bf16,
-                     max_threads, ORACLE_SRC)
+                     max_threads, ORACLE_SRC, INDEX_FLOOR, INDEX_TRUNC)
 
 __all__ = ["build", "load", "backproject", "backproject_voxels", "round_f16", "round_bf16",
-           "max_threads", "ORACLE_SRC"]
+           "max_threads", "ORACLE_SRC", "INDEX_FLOOR", "INDEX_TRUNC"]

@@ -44,10 +44,10 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     p_f = ctypes.POINTER(ctypes.c_float)
     p_i64 = ctypes.POINTER(ctypes.c_int64)
     lib.rct_oracle_backproject.argtypes = [c_int, c_int, c_int, c_int, p_d, p_d, p_d, p_f,
-                                           c_int, c_int, c_int, p_d]
+                                           c_int, c_int, c_int, c_int, p_d]
     lib.rct_oracle_backproject.restype = c_int
     lib.rct_oracle_backproject_voxels.argtypes = [c_int, c_int, c_int, c_int, p_d, p_d, p_d, p_f,
-                                                  p_i64, c_i64, c_int, p_d]
+                                                  p_i64, c_i64, c_int, c_int, p_d]
     lib.rct_oracle_backproject_voxels.restype = c_int
     lib.rct_oracle_round_f16.argtypes = [p_f, p_f, c_i64]
     lib.rct_oracle_round_f16.restype = c_int
@@ -84,9 +84,13 @@ def _prep(matrices, origin, spacing, proj, W, H):
     return A, o, s, p, n
 
 
+INDEX_FLOOR, INDEX_TRUNC = 0, 1
+
+
 def backproject(L, W, H, matrices, origin, spacing, proj, *, z_range=None, n_threads=1,
-                vol=None, lib=None) -> np.ndarray:
-    """FP64 backprojection of all given views; returns (nz, L, L) float64 (accumulated into ``vol``)."""
+                vol=None, lib=None, index_rule=INDEX_FLOOR) -> np.ndarray:
+    """FP64 backprojection of all given views; returns (nz, L, L) float64 (accumulated into ``vol``).
+    ``index_rule`` INDEX_TRUNC takes Listing 1's truncating (int) cast for the cell instead of floor."""
     lib = lib or load()
     A, o, s, p, n = _prep(matrices, origin, spacing, proj, W, H)
     z0, z1 = (0, L) if z_range is None else z_range
@@ -96,14 +100,14 @@ def backproject(L, W, H, matrices, origin, spacing, proj, *, z_range=None, n_thr
         raise ValueError("vol must be a C-contiguous float64 array of the slab's size")
     rc = lib.rct_oracle_backproject(L, W, H, n, _ptr(A, ctypes.c_double), _ptr(o, ctypes.c_double),
                                     _ptr(s, ctypes.c_double), _ptr(p, ctypes.c_float),
-                                    z0, z1, n_threads, _ptr(vol, ctypes.c_double))
+                                    z0, z1, n_threads, index_rule, _ptr(vol, ctypes.c_double))
     if rc != 0:
         raise RuntimeError(f"rct_oracle_backproject failed with code {rc}")
     return vol
 
 
 def backproject_voxels(L, W, H, matrices, origin, spacing, proj, flat_idx, *, n_threads=1,
-                       lib=None) -> np.ndarray:
+                       lib=None, index_rule=INDEX_FLOOR) -> np.ndarray:
     """FP64 sums for the voxels with flat indices ``flat_idx`` (z*L*L + y*L + x)."""
     lib = lib or load()
     A, o, s, p, n = _prep(matrices, origin, spacing, proj, W, H)
@@ -112,7 +116,7 @@ def backproject_voxels(L, W, H, matrices, origin, spacing, proj, flat_idx, *, n_
     rc = lib.rct_oracle_backproject_voxels(L, W, H, n, _ptr(A, ctypes.c_double),
                                            _ptr(o, ctypes.c_double), _ptr(s, ctypes.c_double),
                                            _ptr(p, ctypes.c_float), _ptr(idx, ctypes.c_int64),
-                                           idx.size, n_threads, _ptr(out, ctypes.c_double))
+                                           idx.size, n_threads, index_rule, _ptr(out, ctypes.c_double))
     if rc != 0:
         raise RuntimeError(f"rct_oracle_backproject_voxels failed with code {rc}")
     return out

@@ -27,10 +27,13 @@
  * design notes):
  *   - The listing truncates with an (int) cast.  That equals floor only for
  *     non-negative coordinates; for ix in (-1, 0) truncation would give
- *     i0 = 0 and a negative weight.  The oracle uses floor: the image is then
- *     the zero-extended grid, and the interpolant is continuous everywhere
- *     (this is also what the paper's zero-padded projection buffer, Section
- *     "SIMD Vectorization", computes).
+ *     i0 = 0 and a negative weight.  The oracle uses floor by default: the
+ *     image is then the zero-extended grid, and the interpolant is continuous
+ *     everywhere (this is also what the paper's zero-padded projection buffer,
+ *     Section "SIMD Vectorization", computes).  index_rule = 1 takes the
+ *     listing's truncation instead (RabbitCT compatibility): the cell is
+ *     trunc(ix), and fx = ix - trunc(ix) is negative for negative ix, so the
+ *     lerp extrapolates from the two taps at the image edge.
  *   - The listing's bound tests compare the row index with `width` and the
  *     column index with `height`, while it addresses rows with stride
  *     `width`.  The oracle tests the column index against W and the row
@@ -60,9 +63,12 @@
 #define ORACLE_EINVAL 1
 #define ORACLE_EBEHIND 2   /* larger codes win when several planes report */
 
+#define ORACLE_INDEX_FLOOR 0
+#define ORACLE_INDEX_TRUNC 1   /* the listing's (int) cast: toward zero (RabbitCT compatibility) */
+
 /* One voxel, one view: returns the update val / w^2 of Listing 1 (Parts 1-3). */
 static int oracle_update(const double *A, const float *img, int W, int H,
-                         double wx, double wy, double wz, double *out)
+                         double wx, double wy, double wz, int index_rule, double *out)
 {
     /* Part 1: projection and de-homogenisation */
     double u = A[0] * wx + A[1] * wy + A[2] * wz + A[3];
@@ -73,6 +79,10 @@ static int oracle_update(const double *A, const float *img, int W, int H,
     double iy = v / w;
     double fi0 = floor(ix);
     double fj0 = floor(iy);
+    if (index_rule == ORACLE_INDEX_TRUNC) {     /* (int) ix: toward zero, so fx < 0 for negative ix */
+        fi0 = trunc(ix);
+        fj0 = trunc(iy);
+    }
     double fx = ix - fi0;
     double fy = iy - fj0;
 
@@ -118,10 +128,11 @@ static int check_args(int L, int W, int H, int n_views, const double *A, const d
  */
 int rct_oracle_backproject(int L, int W, int H, int n_views, const double *A,
                            const double *origin, const double *spacing, const float *proj,
-                           int z_begin, int z_end, int n_threads, double *vol)
+                           int z_begin, int z_end, int n_threads, int index_rule, double *vol)
 {
     int rc = check_args(L, W, H, n_views, A, origin, spacing, proj);
     if (rc) return rc;
+    if (index_rule != ORACLE_INDEX_FLOOR && index_rule != ORACLE_INDEX_TRUNC) return ORACLE_EINVAL;
     if (z_begin < 0 || z_end > L || z_begin > z_end || !vol) return ORACLE_EINVAL;
     int status = ORACLE_OK;
     const long img_px = (long)W * H;
@@ -140,7 +151,7 @@ int rct_oracle_backproject(int L, int W, int H, int n_views, const double *A,
                 for (int x = 0; x < L; ++x) {
                     double wx = origin[0] + x * spacing[0];
                     double upd;
-                    if (oracle_update(Ai, img, W, H, wx, wy, wz, &upd) != ORACLE_OK) {
+                    if (oracle_update(Ai, img, W, H, wx, wy, wz, index_rule, &upd) != ORACLE_OK) {
                         status = ORACLE_EBEHIND;
                         continue;
                     }
@@ -159,10 +170,12 @@ int rct_oracle_backproject(int L, int W, int H, int n_views, const double *A,
  */
 int rct_oracle_backproject_voxels(int L, int W, int H, int n_views, const double *A,
                                   const double *origin, const double *spacing, const float *proj,
-                                  const int64_t *idx, int64_t n_idx, int n_threads, double *out)
+                                  const int64_t *idx, int64_t n_idx, int n_threads, int index_rule,
+                                  double *out)
 {
     int rc = check_args(L, W, H, n_views, A, origin, spacing, proj);
     if (rc) return rc;
+    if (index_rule != ORACLE_INDEX_FLOOR && index_rule != ORACLE_INDEX_TRUNC) return ORACLE_EINVAL;
     if (n_idx < 0 || (n_idx > 0 && (!idx || !out))) return ORACLE_EINVAL;
     const long img_px = (long)W * H;
     const int64_t total = (int64_t)L * L * L;
@@ -182,7 +195,7 @@ int rct_oracle_backproject_voxels(int L, int W, int H, int n_views, const double
         double acc = out[k];
         for (int i = 0; i < n_views; ++i) {
             double upd;
-            if (oracle_update(A + 12L * i, proj + img_px * i, W, H, wx, wy, wz, &upd) != ORACLE_OK) {
+            if (oracle_update(A + 12L * i, proj + img_px * i, W, H, wx, wy, wz, index_rule, &upd) != ORACLE_OK) {
                 status = ORACLE_EBEHIND;
                 continue;
             }

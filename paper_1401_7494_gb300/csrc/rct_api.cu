@@ -99,6 +99,7 @@ struct rct_ctx {
     int dtype = DT_F32;
     int interp = RCT_INTERP_SOFT;
     int frame = RCT_FRAME_GLOBAL;
+    int index_rule = RCT_INDEX_FLOOR;
     rct_tuning tune{};              // gather may be RCT_GATHER_AUTO here
     bool tune_explicit_gather = false;
 
@@ -132,11 +133,15 @@ namespace {
 
 int kernel_kind(const rct_ctx *c) { return c->interp == RCT_INTERP_TEX ? G_TEXLIN : G_SOFT; }
 
+// The gather route the kernels use: the tuned one, except that the truncating index rule reads the
+// caller's images with plain loads.
+int gather_of(const rct_ctx *c) { return c->index_rule == RCT_INDEX_TRUNC ? RCT_GATHER_LDG : c->tune.gather; }
+
 // Number of z positions of each run that fetch through the texture gather (the rest load).
 // LDG, QUAD: none; TLD4 (and AUTO): all; MIX: the tuned split.
 int tex_zrun_of(const rct_ctx *c) {
     const int R = c->tune.zrun;
-    switch (c->tune.gather) {
+    switch (gather_of(c)) {
         case RCT_GATHER_LDG:
         case RCT_GATHER_QUAD:
         case RCT_GATHER_PAIR: return 0;
@@ -150,8 +155,8 @@ bool uses_tex(const rct_ctx *c) { return kernel_kind(c) == G_TEXLIN || tex_zrun_
 // Staged layout the load part of the software route reads: 0 = none (texture only, or the
 // caller's linear image), 1 = quads (QUAD, MIX), 2 = vertical pairs (PAIR).
 int load_layout(const rct_ctx *c) {
-    if (kernel_kind(c) != G_SOFT || c->tune.gather == RCT_GATHER_LDG || tex_zrun_of(c) >= c->tune.zrun) return 0;
-    return c->tune.gather == RCT_GATHER_PAIR ? 2 : 1;
+    if (kernel_kind(c) != G_SOFT || gather_of(c) == RCT_GATHER_LDG || tex_zrun_of(c) >= c->tune.zrun) return 0;
+    return gather_of(c) == RCT_GATHER_PAIR ? 2 : 1;
 }
 
 bool uses_quad(const rct_ctx *c) { return load_layout(c) != 0; }
@@ -169,7 +174,7 @@ cudaError_t launch_stage_layout(const rct_ctx *c, const void *src, void *dst, cu
 // filtered texture.
 bool uses_linear(const rct_ctx *c) {
     if (kernel_kind(c) == G_TEXLIN) return c->dtype == DT_BF16;
-    return c->tune.gather == RCT_GATHER_LDG;
+    return gather_of(c) == RCT_GATHER_LDG;
 }
 
 // Host input must land in linear device memory first when a kernel or a staging step reads it there.
@@ -305,6 +310,7 @@ LaunchConfig launch_config(const rct_ctx *c, int kind) {
     lc.bx = c->tune.block_x;
     lc.by = c->tune.block_y;
     lc.frame = (kind == G_SOFT && c->frame == RCT_FRAME_BLOCK) ? 1 : 0;
+    lc.trunc = (kind == G_SOFT && c->index_rule == RCT_INDEX_TRUNC) ? 1 : 0;
     return lc;
 }
 
@@ -356,6 +362,8 @@ cudaError_t launch(rct_ctx *c, const LaunchConfig &lc, const BpParams &p, cudaSt
     c->launches += 1;
     if (lc.gather == G_TEXLIN) {
         e = launch_bp_texlin(lc, p, s);
+    } else if (lc.trunc) {
+        e = lc.dtype == DT_F32 ? launch_bp_soft_f32_trunc(lc, p, s) : cudaErrorInvalidValue;
     } else {
         switch (lc.dtype) {
             case DT_F32: e = launch_bp_soft_f32(lc, p, s); break;
@@ -570,6 +578,8 @@ rct_status rct_set_precision(rct_ctx *c, int proj_dtype, int interp) {
     if (interp != RCT_INTERP_SOFT && interp != RCT_INTERP_TEX) return fail(RCT_EINVAL, "unknown interp %d", interp);
     if (c->frame == RCT_FRAME_BLOCK && (proj_dtype != RCT_PROJ_F32 || interp != RCT_INTERP_SOFT))
         return fail(RCT_ENOTSUP, "block frames need FP32 projections and software interpolation");
+    if (c->index_rule == RCT_INDEX_TRUNC && (proj_dtype != RCT_PROJ_F32 || interp != RCT_INTERP_SOFT))
+        return fail(RCT_ENOTSUP, "the truncating index rule needs FP32 projections and software interpolation");
     c->dtype = proj_dtype;
     c->interp = interp;
     return RCT_OK;
@@ -580,8 +590,38 @@ rct_status rct_set_frame(rct_ctx *c, int frame) {
     if (frame != RCT_FRAME_GLOBAL && frame != RCT_FRAME_BLOCK) return fail(RCT_EINVAL, "unknown frame %d", frame);
     if (frame == RCT_FRAME_BLOCK && (c->dtype != DT_F32 || c->interp != RCT_INTERP_SOFT))
         return fail(RCT_ENOTSUP, "block frames need FP32 projections and software interpolation");
+    if (frame == RCT_FRAME_BLOCK && c->index_rule == RCT_INDEX_TRUNC)
+        return fail(RCT_ENOTSUP, "the truncating index rule runs in the global frame");
     c->frame = frame;
     return RCT_OK;
+}
+
+rct_status rct_set_index_rule(rct_ctx *c, int rule) {
+    if (!c) return fail(RCT_EINVAL, "null context");
+    if (rule != RCT_INDEX_FLOOR && rule != RCT_INDEX_TRUNC) return fail(RCT_EINVAL, "unknown index rule %d", rule);
+    if (rule == RCT_INDEX_TRUNC && (c->dtype != DT_F32 || c->interp != RCT_INTERP_SOFT || c->frame != RCT_FRAME_GLOBAL))
+        return fail(RCT_ENOTSUP, "the truncating index rule needs FP32 projections, software interpolation and the "
+                                 "global frame");
+    c->index_rule = rule;
+    return RCT_OK;
+}
+
+rct_status rct_get_index_rule(const rct_ctx *c, int *rule) {
+    if (!c || !rule) return fail(RCT_EINVAL, "null pointer");
+    *rule = c->index_rule;
+    return RCT_OK;
+}
+
+rct_status rct_set_geometry_rabbitct(rct_ctx *c, const float *matrices, float O, float MM) {
+    if (!c) return fail(RCT_EINVAL, "null context");
+    if (!matrices) return fail(RCT_EINVAL, "null matrices");
+    std::vector<double> rm(12 * (size_t)c->n_views);
+    for (int v = 0; v < c->n_views; ++v)
+        for (int r = 0; r < 3; ++r)
+            for (int col = 0; col < 4; ++col)
+                rm[12 * (size_t)v + 4 * r + col] = static_cast<double>(matrices[12 * (size_t)v + 3 * col + r]);
+    const double origin[3] = {O, O, O}, spacing[3] = {MM, MM, MM};
+    return rct_set_geometry(c, rm.data(), origin, spacing);
 }
 
 rct_status rct_get_frame(const rct_ctx *c, int *frame) {

@@ -253,9 +253,12 @@ __device__ __forceinline__ void block_frame(const ViewGeo *vg, float bX, float b
 
 // FRAME: block frames (needs p.geo) instead of the global frame; the texture-filtered kernel
 // always takes the global frame (the texture unit needs absolute coordinates).
-template <int G, int DT, int XV, int R, int ROUTE, bool FRAME>
+// TRUNC: the cell index of Listing 1's (int) cast, which truncates toward zero, instead of floor
+// (RabbitCT compatibility; plain loads only).
+template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = false>
 __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParams p) {
     static_assert(!FRAME || G == G_SOFT, "block frames are for the software gathers");
+    static_assert(!TRUNC || (G == G_SOFT && ROUTE == ROUTE_LDG && !FRAME), "truncation: global frame, plain loads");
     const int L = p.L;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * XV;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -361,9 +364,10 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
                     const float2 uv = __ffma2_rn(make_float2(fj, fj), m_x, __ffma2_rn(make_float2(fr, fr), c.m_z, buv));
                     const float w = fmaf(fj, mw[0], fmaf(fr, c.w_z, bw));
                     const int2 ci = cell_index(c, uv, w);
-                    left = left && ci.x < 0;
+                    // (a truncated cell of a coordinate in (-2, -1) still has its right tap on column 0)
+                    left = left && ci.x < (TRUNC ? -1 : 0);
                     right = right && ci.x > p.W;
-                    top = top && ci.y < 0;
+                    top = top && ci.y < (TRUNC ? -1 : 0);
                     bottom = bottom && ci.y > p.H;
                 }
             }
@@ -388,6 +392,14 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
                 } else {
                     float2 t, f;
                     floor_frac(uv, rw, t, f);
+                    if constexpr (TRUNC) {
+                        // (int) of a negative coordinate with a fraction is floor + 1: the cell moves one
+                        // pixel right and its fraction becomes f - 1 (the listing then extrapolates).
+                        const float ax = (__float_as_int(t.x) <= c.qcx && f.x != 0.0f) ? 1.0f : 0.0f;
+                        const float ay = (__float_as_int(t.y) <= c.qcy && f.y != 0.0f) ? 1.0f : 0.0f;
+                        t = __fadd2_rn(t, make_float2(ax, ay));
+                        f = __fadd2_rn(f, make_float2(-ax, -ay));
+                    }
                     if constexpr (ROUTE == ROUTE_TEX) {
                         accumulate_tex<DT>(c, t, f, w2, acc[r][j]);
                     } else if constexpr (ROUTE == ROUTE_LDG) {
@@ -419,24 +431,24 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
     }
 }
 
-template <int G, int DT, int XV, int R, int ROUTE, bool FRAME>
+template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = false>
 cudaError_t launch_one(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     if (FRAME && !p.geo) return cudaErrorInvalidValue;
     const int gx = (p.L / XV + c.bx - 1) / c.bx;
     const dim3 grid(gx, (p.L + c.by - 1) / c.by, (p.L + R - 1) / R);
-    bp_kernel<G, DT, XV, R, ROUTE, FRAME><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
+    bp_kernel<G, DT, XV, R, ROUTE, FRAME, TRUNC><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
     return cudaGetLastError();
 }
 
-template <int G, int DT, int XV, int ROUTE, bool FRAME>
+template <int G, int DT, int XV, int ROUTE, bool FRAME, bool TRUNC = false>
 cudaError_t dispatch_r(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     switch (c.zrun) {
-        case 1: return launch_one<G, DT, XV, 1, ROUTE, FRAME>(c, p, s);
-        case 2: return launch_one<G, DT, XV, 2, ROUTE, FRAME>(c, p, s);
-        case 4: return launch_one<G, DT, XV, 4, ROUTE, FRAME>(c, p, s);
-        case 8: return launch_one<G, DT, XV, 8, ROUTE, FRAME>(c, p, s);
+        case 1: return launch_one<G, DT, XV, 1, ROUTE, FRAME, TRUNC>(c, p, s);
+        case 2: return launch_one<G, DT, XV, 2, ROUTE, FRAME, TRUNC>(c, p, s);
+        case 4: return launch_one<G, DT, XV, 4, ROUTE, FRAME, TRUNC>(c, p, s);
+        case 8: return launch_one<G, DT, XV, 8, ROUTE, FRAME, TRUNC>(c, p, s);
         case 16:
-            if constexpr (XV <= 2) return launch_one<G, DT, XV, 16, ROUTE, FRAME>(c, p, s);
+            if constexpr (XV <= 2) return launch_one<G, DT, XV, 16, ROUTE, FRAME, TRUNC>(c, p, s);
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
@@ -446,11 +458,21 @@ cudaError_t dispatch_r(const LaunchConfig &c, const BpParams &p, cudaStream_t s)
 template <int G, int DT, int ROUTE>
 cudaError_t dispatch_xv(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     constexpr bool kFrames = (G == G_SOFT && DT == DT_F32);
-    if (c.frame && !kFrames) return cudaErrorInvalidValue;
+    if ((c.frame && !kFrames) || c.trunc) return cudaErrorInvalidValue;
     switch (c.xv) {
         case 1: return c.frame ? dispatch_r<G, DT, 1, ROUTE, kFrames>(c, p, s) : dispatch_r<G, DT, 1, ROUTE, false>(c, p, s);
         case 2: return c.frame ? dispatch_r<G, DT, 2, ROUTE, kFrames>(c, p, s) : dispatch_r<G, DT, 2, ROUTE, false>(c, p, s);
         case 4: return c.frame ? dispatch_r<G, DT, 4, ROUTE, kFrames>(c, p, s) : dispatch_r<G, DT, 4, ROUTE, false>(c, p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// RabbitCT compatibility (truncating cell index): FP32, global frame, plain loads from the caller's images.
+inline cudaError_t dispatch_trunc(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
+    switch (c.xv) {
+        case 1: return dispatch_r<G_SOFT, DT_F32, 1, ROUTE_LDG, false, true>(c, p, s);
+        case 2: return dispatch_r<G_SOFT, DT_F32, 2, ROUTE_LDG, false, true>(c, p, s);
+        case 4: return dispatch_r<G_SOFT, DT_F32, 4, ROUTE_LDG, false, true>(c, p, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -78,6 +78,7 @@ struct LaunchConfig {
     int zrun;    // voxels per thread along z: 1, 2, 4, 8
     int bx, by;  // block shape
     int frame;   // 1: block frames (FP32 software gathers only; BpParams::geo set)
+    int trunc;   // 1: Listing 1's truncating cell index (FP32, plain loads, global frame)
 };
 
 // Kernel launchers (one translation unit per gather kind).
@@ -85,6 +86,7 @@ cudaError_t launch_bp_soft_f32(const LaunchConfig &c, const BpParams &p, cudaStr
 cudaError_t launch_bp_soft_f16(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
 cudaError_t launch_bp_soft_bf16(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
 cudaError_t launch_bp_texlin(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
+cudaError_t launch_bp_soft_f32_trunc(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
 
 cudaError_t launch_convert(const float *src, void *dst, size_t n, int dtype, cudaStream_t s);
 // Build the zero-padded quad image of one view (see ViewParams) from its linear image.

@@ -21,6 +21,7 @@ RCT_OK, RCT_EINVAL, RCT_ENOMEM, RCT_ECUDA, RCT_ESTATE, RCT_ETIMEOUT, RCT_ENOTSUP
 RCT_PROJ_F32, RCT_PROJ_F16, RCT_PROJ_BF16 = 0, 1, 2
 RCT_INTERP_SOFT, RCT_INTERP_TEX = 0, 1
 RCT_FRAME_GLOBAL, RCT_FRAME_BLOCK = 0, 1
+RCT_INDEX_FLOOR, RCT_INDEX_TRUNC = 0, 1
 RCT_GATHER_AUTO, RCT_GATHER_LDG, RCT_GATHER_TLD4, RCT_GATHER_MIX, RCT_GATHER_QUAD, RCT_GATHER_PAIR = 0, 1, 2, 3, 4, 5
 RCT_MAX_VIEWS_PER_PASS = 32
 STATUS_NAMES = {0: "RCT_OK", 1: "RCT_EINVAL", 2: "RCT_ENOMEM", 3: "RCT_ECUDA", 4: "RCT_ESTATE",
@@ -55,6 +56,9 @@ SIGNATURES = {
     "rct_set_precision": (_I, [_P, _I, _I]),
     "rct_set_frame": (_I, [_P, _I]),
     "rct_get_frame": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "rct_set_index_rule": (_I, [_P, _I]),
+    "rct_get_index_rule": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "rct_set_geometry_rabbitct": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float]),
     "rct_set_tuning": (_I, [_P, ctypes.POINTER(rct_tuning)]),
     "rct_get_tuning": (_I, [_P, ctypes.POINTER(rct_tuning)]),
     "rct_reset_volume": (_I, [_P, _P]),
@@ -182,6 +186,24 @@ def rct_get_frame(ctx) -> int:
     f = ctypes.c_int()
     _check(lib().rct_get_frame(ctx, ctypes.byref(f)))
     return f.value
+
+
+def rct_set_index_rule(ctx, rule: int) -> None:
+    _check(lib().rct_set_index_rule(ctx, int(rule)))
+
+
+def rct_get_index_rule(ctx) -> int:
+    r = ctypes.c_int()
+    _check(lib().rct_get_index_rule(ctx, ctypes.byref(r)))
+    return r.value
+
+
+def rct_set_geometry_rabbitct(ctx, matrices_colmajor, O: float, MM: float) -> None:
+    m = np.ascontiguousarray(np.asarray(matrices_colmajor, dtype=np.float32).reshape(-1))
+    if m.size % 12:
+        raise ValueError("matrices must hold 12 values per view")
+    _check(lib().rct_set_geometry_rabbitct(ctx, m.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                           ctypes.c_float(O), ctypes.c_float(MM)))
 
 
 def rct_set_tuning(ctx, views_per_pass=0, zrun=0, xvec=0, block_x=0, block_y=0, gather=0, tex_zrun=0) -> None:
@@ -352,6 +374,10 @@ class Backprojector:
 
     def set_frame(self, frame=RCT_FRAME_GLOBAL):
         rct_set_frame(self.ctx, frame)
+        return self
+
+    def set_index_rule(self, rule=RCT_INDEX_FLOOR):
+        rct_set_index_rule(self.ctx, rule)
         return self
 
     def set_tuning(self, **kw):

@@ -52,7 +52,8 @@ def oracle_inputs(proj_f32_host: np.ndarray, dtype: str) -> np.ndarray:
 
 
 def gpu_backproject(w: synth.Workload, proj_dev: torch.Tensor, *, dtype="f32", interp=rct.RCT_INTERP_SOFT,
-                    tuning=None, first=0, n=None, chunks=None, frame=rct.RCT_FRAME_GLOBAL) -> np.ndarray:
+                    tuning=None, first=0, n=None, chunks=None, frame=rct.RCT_FRAME_GLOBAL,
+                    index_rule=rct.RCT_INDEX_FLOOR) -> np.ndarray:
     """Backproject through the C ABI; returns the volume as (L, L, L) float32 numpy."""
     n = w.n_views if n is None else n
     stream = torch.cuda.current_stream()
@@ -60,6 +61,7 @@ def gpu_backproject(w: synth.Workload, proj_dev: torch.Tensor, *, dtype="f32", i
         bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
         bp.set_precision(DTYPES[dtype][0], interp)
         bp.set_frame(frame)
+        bp.set_index_rule(index_rule)
         if tuning:
             bp.set_tuning(**tuning)
         data = stored(proj_dev, dtype)
@@ -72,8 +74,9 @@ def gpu_backproject(w: synth.Workload, proj_dev: torch.Tensor, *, dtype="f32", i
         return out.cpu().numpy()
 
 
-def oracle_volume(w: synth.Workload, proj_host: np.ndarray, first=0, n=None, threads=None) -> np.ndarray:
+def oracle_volume(w: synth.Workload, proj_host: np.ndarray, first=0, n=None, threads=None,
+                  index_rule=oracle.INDEX_FLOOR) -> np.ndarray:
     n = w.n_views if n is None else n
     threads = threads or oracle.max_threads()
     return oracle.backproject(w.L, w.geom.det_w, w.geom.det_h, w.geom.matrices[first:first + n], w.origin,
-                              w.spacing, proj_host, n_threads=threads)
+                              w.spacing, proj_host, n_threads=threads, index_rule=index_rule)

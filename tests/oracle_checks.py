@@ -256,7 +256,52 @@ def check_zslab(lib):
     assert np.array_equal(slab, vol[2:5]), "z-slab differs from the full volume"
 
 
+def check_trunc_orthographic(lib):
+    """Listing 1's truncating cell: with w == 1 and pixel = voxel + (-1.25, 2), column x = 1 sits at
+    ix = -0.25, truncated to cell 0 with fx = -0.25, so a constant image extrapolates to itself; column
+    x = 0 sits at ix = -1.25, cell -1, so only tap 0 contributes, with weight ix + 1 = -0.25.  Floor
+    gives 0.75 c and 0 there."""
+    W, H, L = 6, 5, 8
+    cval = 2.0
+    img = np.full((1, H, W), cval, np.float32)
+    origin, spacing = np.zeros(3), np.ones(3)
+    mat = synth.orthographic_matrix(origin, spacing, (-1.25, 2.0))[None]
+    ft = oracle.backproject(L, W, H, mat, origin, spacing, img, lib=lib, index_rule=oracle.INDEX_TRUNC)
+    ff = oracle.backproject(L, W, H, mat, origin, spacing, img, lib=lib)
+    rows = slice(0, H - 3)                      # iy = y + 2 keeps both tap rows on the image
+    assert np.all(ft[:, rows, 1] == cval), "truncated cell at ix = -0.25 must extrapolate the constant"
+    assert np.all(ft[:, rows, 0] == -0.25 * cval), "truncated cell at ix = -1.25 must weight tap 0 by -0.25"
+    assert np.all(ff[:, rows, 1] == 0.75 * cval) and np.all(ff[:, rows, 0] == 0.0), "floor reference changed"
+
+
+def check_trunc_affine_extrapolation(lib):
+    """Truncation keeps the cell on the image for ix in (-1, 0) (and iy), where the lerp of an affine
+    image I = a + b i + c j extrapolates it exactly; elsewhere inside it agrees with floor."""
+    geom = _small_geom(6, seed=5)
+    L = 9
+    origin, spacing = synth.volume_grid(L)
+    W, H = geom.det_w, geom.det_h
+    a, b, c = 0.5, 0.25, -0.125
+    jj, ii = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    img = (a + b * ii + c * jj).astype(np.float32)
+    X = voxel_world(L, origin, spacing)
+    n_band = 0
+    for k in range(geom.n_views):
+        ft = oracle.backproject(L, W, H, geom.matrices[k:k + 1], origin, spacing, img[None], lib=lib,
+                                index_rule=oracle.INDEX_TRUNC)
+        ff = _run(lib, L, W, H, geom.matrices[k:k + 1], origin, spacing, img[None])
+        ix, iy, w = pinhole(geom, k, X)
+        eps = 1e-6
+        cover = (ix > -1 + eps) & (ix < W - 1 - eps) & (iy > -1 + eps) & (iy < H - 1 - eps)
+        band = cover & ((ix < -eps) | (iy < -eps))
+        n_band += int(band.sum())
+        _close(ft[cover], ((a + b * ix + c * iy) / (w * w))[cover], 1e-12, "truncated cell, affine image")
+        nonneg = (ix > eps) & (iy > eps)
+        assert np.array_equal(ft[nonneg], ff[nonneg]), "truncation and floor differ at non-negative coordinates"
+    assert n_band > 10, "truncation check saw too few voxels in the negative band"
+
+
 ALL_CHECKS = [check_orthographic_identity, check_orthographic_shift, check_cone_beam_scipy,
               check_tent_brute_force, check_affine_image, check_constant_image,
               check_isocentre_delta, check_linearity, check_view_additivity,
-              check_voxel_subset, check_zslab]
+              check_voxel_subset, check_zslab, check_trunc_orthographic, check_trunc_affine_extrapolation]

@@ -43,6 +43,10 @@ MUTATIONS = {
     # voxel corner instead of voxel centre
     "half_voxel": [("double wx = origin[0] + x * spacing[0];\n                    double upd;",
                     "double wx = origin[0] + (x + 0.5) * spacing[0];\n                    double upd;")],
+    # the truncating index rule falls back to floor
+    "trunc_as_floor": [("        fi0 = trunc(ix);\n        fj0 = trunc(iy);", "        fi0 = floor(ix);\n        fj0 = floor(iy);")],
+    # the truncating index rule rounds to nearest instead of toward zero
+    "trunc_as_round": [("        fi0 = trunc(ix);\n        fj0 = trunc(iy);", "        fi0 = round(ix);\n        fj0 = round(iy);")],
     # last view dropped
     "dropped_view": [("for (int i = 0; i < n_views; ++i) {\n        const double *Ai", "for (int i = 0; i + 1 < n_views; ++i) {\n        const double *Ai")],
     # weights swapped within a lerp: (fx) on the left tap
