@@ -188,6 +188,34 @@ RCT_API rct_status rct_set_index_rule(rct_ctx *ctx, int rule);
 RCT_API rct_status rct_get_index_rule(const rct_ctx *ctx, int *rule);
 RCT_API rct_status rct_set_geometry_rabbitct(rct_ctx *ctx, const float *matrices, float O, float MM);
 
+/*
+ * Pre-processing of raw projections on the device (the step before the path: RabbitCT supplies
+ * projections already weighted and filtered, Section "RabbitCT Benchmark"; a scanner supplies line
+ * integrals).  For view v and pixel (i, j), with D = sdd (source-detector distance, mm),
+ * tau = pitch (detector pixel size, mm) and (u0, v0) the view's principal point (pixels):
+ *
+ *   cosine weight  p'(i, j) = p(i, j) * D / sqrt(D^2 + ((i - u0) tau)^2 + ((j - v0) tau)^2)
+ *   ramp filter    q(i, j)  = tau * sum_{k=0}^{W-1} h[i - k] p'(k, j)
+ *                  h[n]     = -2 / (pi^2 tau^2 (4 n^2 - 1))     (Shepp-Logan kernel, FDK method)
+ *
+ * i.e. each row is convolved linearly (zero outside the row) with the kernel.
+ *
+ * rct_set_filter stores the filter for the context: sdd and pitch (finite, > 0) and principal,
+ * n_views pairs (u0, v0) in view order (copied; the caller's array may be freed on return).
+ * Rows longer than 8192 pixels give RCT_ENOTSUP.  It synchronises the device (set-up call).
+ *
+ * rct_filter_projections filters views [first_view, first_view + n): d_raw holds n FP32 images
+ * [n][H][W] on the device; d_out receives n images in out_dtype (rct_proj_dtype, rounded to
+ * nearest even for 16-bit types), the layout rct_backproject reads.  An FP32 output may be
+ * written in place (d_out == d_raw); any other overlap of input and output is RCT_EINVAL.
+ * Enqueued on `stream`; the caller keeps both buffers valid until the stream reaches the call.
+ * RCT_ESTATE before rct_set_filter.  The arithmetic is FP32 (transforms of length >= 2W - 1 in
+ * shared memory, see the design notes); the spectrum of h is computed on the host in FP64.
+ */
+RCT_API rct_status rct_set_filter(rct_ctx *ctx, double sdd, double pitch, const double *principal);
+RCT_API rct_status rct_filter_projections(rct_ctx *ctx, const float *d_raw, void *d_out, int out_dtype,
+                                          int first_view, int n, void *stream);
+
 /* Override the kernel tuning (see rct_tuning).  Validated synchronously. */
 RCT_API rct_status rct_set_tuning(rct_ctx *ctx, const rct_tuning *t);
 /* Read the tuning the next launch will use (after AUTO resolution). */

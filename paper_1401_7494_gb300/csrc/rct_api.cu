@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -40,6 +41,8 @@ rct_status cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 size_t dtype_size(int dt) { return dt == DT_F32 ? 4 : 2; }
+
+constexpr double kPi = 3.14159265358979323846;
 
 // One staging slot: a 2D CUDA array that holds one view for texture sampling.
 struct Slot {
@@ -93,6 +96,12 @@ struct rct_ctx {
 
     bool geometry_set = false;
     ViewGeo *geo_dev = nullptr;     // n_views block-frame geometries on the device
+
+    bool filter_set = false;        // cosine weight + ramp filter of raw projections (rct_set_filter)
+    FilterParams filt{};
+    float2 *filt_twiddle = nullptr;
+    float *filt_spectrum = nullptr;
+    float2 *filt_principal = nullptr;
     std::vector<double> fold;       // n_views x 12, FP64: rows u', v', w over centred voxel coords
     std::vector<int> shift;         // n_views x 2: integer detector shift (cu, cv)
 
@@ -418,6 +427,27 @@ rct_status ensure_host_staging(rct_ctx *c) {
     return RCT_OK;
 }
 
+// In-place iterative radix-2 DFT, X[k] = sum_n x[n] exp(-2 pi i k n / N), FP64 (host set-up only).
+void host_fft(std::vector<std::complex<double>> &a) {
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        const double ang = -2.0 * kPi / static_cast<double>(len);
+        for (size_t i = 0; i < n; i += len)
+            for (size_t k = 0; k < len / 2; ++k) {
+                const std::complex<double> w(std::cos(ang * k), std::sin(ang * k));
+                const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+    }
+}
+
 rct_status validate_range(const rct_ctx *c, const void *proj, int first, int n) {
     if (!c->geometry_set) return fail(RCT_ESTATE, "rct_set_geometry has not been called");
     if (n < 0) return fail(RCT_EINVAL, "n = %d is negative", n);
@@ -531,6 +561,9 @@ void rct_destroy(rct_ctx *c) {
     if (c->lin_stage) cudaFree(c->lin_stage);
     if (c->quad_buf) cudaFree(c->quad_buf);
     if (c->geo_dev) cudaFree(c->geo_dev);
+    if (c->filt_twiddle) cudaFree(c->filt_twiddle);
+    if (c->filt_spectrum) cudaFree(c->filt_spectrum);
+    if (c->filt_principal) cudaFree(c->filt_principal);
     if (c->widen_buf) cudaFree(c->widen_buf);
     for (int i = 0; i < 2; ++i) {
         if (c->ev_filled[i]) cudaEventDestroy(c->ev_filled[i]);
@@ -593,6 +626,97 @@ rct_status rct_set_frame(rct_ctx *c, int frame) {
     if (frame == RCT_FRAME_BLOCK && c->index_rule == RCT_INDEX_TRUNC)
         return fail(RCT_ENOTSUP, "the truncating index rule runs in the global frame");
     c->frame = frame;
+    return RCT_OK;
+}
+
+rct_status rct_set_filter(rct_ctx *c, double sdd, double pitch, const double *principal) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if (!principal) return fail(RCT_EINVAL, "null principal points");
+    if (!(std::isfinite(sdd) && sdd > 0.0 && std::isfinite(pitch) && pitch > 0.0))
+        return fail(RCT_EINVAL, "source-detector distance and pitch must be finite and positive");
+    for (int v = 0; v < 2 * c->n_views; ++v)
+        if (!std::isfinite(principal[v])) return fail(RCT_EINVAL, "non-finite principal point");
+    if (c->W > 8192) return fail(RCT_ENOTSUP, "ramp filter rows of %d pixels: at most 8192", c->W);
+    int log2n = 4;                       // the transform works in blocks of 16 values per thread
+    while ((1 << log2n) < 2 * c->W - 1) ++log2n;
+    const int N = 1 << log2n;
+    // The kernel h[n] = -2 / (pi^2 pitch^2 (4 n^2 - 1)) for |n| < W, placed circularly; its DFT is
+    // real (h is real and even).  pitch (the convolution's quadrature weight) and 1/N (the inverse
+    // transform's normalisation) are folded in.
+    std::vector<std::complex<double>> hz(N, 0.0);
+    for (int n = 0; n < c->W; ++n) {
+        const double h = -2.0 / (kPi * kPi * pitch * pitch * (4.0 * n * n - 1.0));
+        hz[n] = h;
+        if (n > 0) hz[N - n] = h;
+    }
+    host_fft(hz);
+    std::vector<float> spectrum(N);
+    for (int k = 0; k < N; ++k) spectrum[k] = static_cast<float>(hz[k].real() * pitch / N);
+    std::vector<float2> tw(N);
+    for (int k = 0; k < N; ++k) {
+        const double a = -2.0 * kPi * k / N;
+        tw[k] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+    }
+    std::vector<float2> pp(c->n_views);
+    for (int v = 0; v < c->n_views; ++v)
+        pp[v] = make_float2(static_cast<float>(principal[2 * v]), static_cast<float>(principal[2 * v + 1]));
+    // Filter launches already queued read the old tables: let them finish before they are replaced.
+    RCT_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    if (c->filt_twiddle) cudaFree(c->filt_twiddle);
+    if (c->filt_spectrum) cudaFree(c->filt_spectrum);
+    if (c->filt_principal) cudaFree(c->filt_principal);
+    c->filt_twiddle = nullptr;
+    c->filt_spectrum = nullptr;
+    c->filt_principal = nullptr;
+    c->filter_set = false;
+    if (cudaMalloc(&c->filt_twiddle, sizeof(float2) * N) != cudaSuccess ||
+        cudaMalloc(&c->filt_spectrum, sizeof(float) * N) != cudaSuccess ||
+        cudaMalloc(&c->filt_principal, sizeof(float2) * c->n_views) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(RCT_ENOMEM, "filter table allocation failed");
+    }
+    RCT_CUDA(cudaMemcpy(c->filt_twiddle, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice), "cudaMemcpy");
+    RCT_CUDA(cudaMemcpy(c->filt_spectrum, spectrum.data(), sizeof(float) * N, cudaMemcpyHostToDevice), "cudaMemcpy");
+    RCT_CUDA(cudaMemcpy(c->filt_principal, pp.data(), sizeof(float2) * c->n_views, cudaMemcpyHostToDevice),
+             "cudaMemcpy");
+    c->filt.W = c->W;
+    c->filt.H = c->H;
+    c->filt.log2n = log2n;
+    c->filt.sdd = static_cast<float>(sdd);
+    c->filt.pitch = static_cast<float>(pitch);
+    c->filt.twiddle = c->filt_twiddle;
+    c->filt.spectrum = c->filt_spectrum;
+    c->filt.principal = c->filt_principal;
+    c->filter_set = true;
+    return RCT_OK;
+}
+
+rct_status rct_filter_projections(rct_ctx *c, const float *d_raw, void *d_out, int out_dtype, int first_view, int n,
+                                  void *stream) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if (!c->filter_set) return fail(RCT_ESTATE, "rct_set_filter has not been called");
+    if (out_dtype < RCT_PROJ_F32 || out_dtype > RCT_PROJ_BF16) return fail(RCT_EINVAL, "unknown dtype %d", out_dtype);
+    if (n < 0) return fail(RCT_EINVAL, "n = %d is negative", n);
+    if (first_view < 0 || (long long)first_view + n > c->n_views)
+        return fail(RCT_EINVAL, "views [%d, %lld) outside [0, %d)", first_view, (long long)first_view + n, c->n_views);
+    if (n == 0) return RCT_OK;
+    if (!d_raw || !d_out) return fail(RCT_EINVAL, "null projection pointer");
+    const size_t px = (size_t)c->W * c->H * n;
+    if (out_dtype != RCT_PROJ_F32) {     // a narrower output written in place would overwrite unread input
+        const char *r0 = reinterpret_cast<const char *>(d_raw), *r1 = r0 + px * sizeof(float);
+        const char *o0 = static_cast<const char *>(d_out), *o1 = o0 + px * dtype_size(out_dtype);
+        if (o0 < r1 && r0 < o1) return fail(RCT_EINVAL, "a 16-bit output must not overlap the raw input");
+    } else if (d_out != static_cast<const void *>(d_raw)) {
+        const char *r0 = reinterpret_cast<const char *>(d_raw), *r1 = r0 + px * sizeof(float);
+        const char *o0 = static_cast<const char *>(d_out), *o1 = o0 + px * sizeof(float);
+        if (o0 < r1 && r0 < o1) return fail(RCT_EINVAL, "output overlaps the input without coinciding with it");
+    }
+    FilterParams f = c->filt;
+    f.principal = c->filt_principal + first_view;
+    cudaError_t e = launch_ramp_filter(f, d_raw, d_out, out_dtype, n, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "ramp filter launch");
     return RCT_OK;
 }
 

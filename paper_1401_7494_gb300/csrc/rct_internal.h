@@ -88,6 +88,18 @@ cudaError_t launch_bp_soft_bf16(const LaunchConfig &c, const BpParams &p, cudaSt
 cudaError_t launch_bp_texlin(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
 cudaError_t launch_bp_soft_f32_trunc(const LaunchConfig &c, const BpParams &p, cudaStream_t s);
 
+// Cosine weighting + row-wise ramp filter of raw projections (rct_filter.cu).
+struct FilterParams {
+    int W, H;
+    int log2n;                 // transform length N = 2^log2n >= 2W - 1
+    float sdd, pitch;          // source-detector distance, pixel pitch (mm)
+    const float2 *twiddle;     // N entries exp(-2 pi i k / N)
+    const float *spectrum;     // N entries: the kernel's DFT times pitch / N (real)
+    const float2 *principal;   // (u0, v0) of the first view filtered, then one per view
+};
+cudaError_t launch_ramp_filter(const FilterParams &f, const float *raw, void *out, int out_dtype, int n,
+                               cudaStream_t s);
+
 cudaError_t launch_convert(const float *src, void *dst, size_t n, int dtype, cudaStream_t s);
 // Build the zero-padded quad image of one view (see ViewParams) from its linear image.
 cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s);

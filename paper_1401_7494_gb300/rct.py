@@ -57,6 +57,8 @@ SIGNATURES = {
     "rct_set_frame": (_I, [_P, _I]),
     "rct_get_frame": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "rct_set_index_rule": (_I, [_P, _I]),
+    "rct_set_filter": (_I, [_P, ctypes.c_double, ctypes.c_double, _D3]),
+    "rct_filter_projections": (_I, [_P, _P, _P, _I, _I, _I, _P]),
     "rct_get_index_rule": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "rct_set_geometry_rabbitct": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float]),
     "rct_set_tuning": (_I, [_P, ctypes.POINTER(rct_tuning)]),
@@ -186,6 +188,18 @@ def rct_get_frame(ctx) -> int:
     f = ctypes.c_int()
     _check(lib().rct_get_frame(ctx, ctypes.byref(f)))
     return f.value
+
+
+def rct_set_filter(ctx, sdd: float, pitch: float, principal) -> None:
+    pp = np.ascontiguousarray(np.asarray(principal, dtype=np.float64).reshape(-1))
+    if pp.size % 2:
+        raise ValueError("principal points come in (u0, v0) pairs")
+    _check(lib().rct_set_filter(ctx, float(sdd), float(pitch), pp.ctypes.data_as(_D3)))
+
+
+def rct_filter_projections(ctx, d_raw, d_out, out_dtype: int, first_view: int, n: int, stream=None) -> None:
+    _check(lib().rct_filter_projections(ctx, _addr(d_raw), _addr(d_out), int(out_dtype), first_view, n,
+                                        _stream(stream)))
 
 
 def rct_set_index_rule(ctx, rule: int) -> None:
@@ -379,6 +393,15 @@ class Backprojector:
     def set_index_rule(self, rule=RCT_INDEX_FLOOR):
         rct_set_index_rule(self.ctx, rule)
         return self
+
+    def set_filter(self, sdd, pitch, principal):
+        rct_set_filter(self.ctx, sdd, pitch, principal)
+        return self
+
+    def filter(self, d_raw, d_out, out_dtype=RCT_PROJ_F32, first_view=0, n=None, stream=None):
+        if n is None:
+            n = int(d_raw.shape[0])
+        rct_filter_projections(self.ctx, d_raw, d_out, out_dtype, first_view, n, stream)
 
     def set_tuning(self, **kw):
         rct_set_tuning(self.ctx, **kw)
