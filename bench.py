@@ -496,11 +496,11 @@ def run_ours(args, dist: Dist) -> dict | None:
         torch.cuda.empty_cache()
     if dist.rank == 0 and not args.no_serve:
         from paper_1401_7494_gb300 import serve_bench
-        protocols, host_data = serve_bench.build_protocols(dev)
+        protocols, host_data = serve_bench.build_protocols(dev, raw=True)
         served = {}
-        for mode in ("f32", "f16"):
-            served[mode] = serve_bench.run_mode(mode, protocols, host_data, n_requests=args.serve_requests,
-                                                log=lambda *_: None)
+        for mode, raw in (("f32", False), ("f16", False), ("f16", True)):
+            served[mode + ("_raw_ingest" if raw else "")] = serve_bench.run_mode(
+                mode, protocols, host_data, n_requests=args.serve_requests, raw=raw, log=lambda *_: None)
         result["served"] = {m: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
                             for m, r in served.items()}
         del host_data

@@ -24,19 +24,23 @@ L_CHOICES = (128, 256, 512, 1024)
 L_WEIGHTS = (0.4, 0.3, 0.2, 0.1)
 
 
-def build_protocols(device, det_w=1248, det_h=960, seed=1405):
-    """Scan protocols (geometry) and pinned host projections of a seeded phantom for each."""
+def build_protocols(device, det_w=1248, det_h=960, seed=1405, raw=False):
+    """Scan protocols (geometry) and pinned host projections of a seeded phantom for each: filtered
+    (key: protocol name) and, with ``raw``, the raw line integrals too (key: name + "/raw")."""
     import torch
     import synth
     protocols, host = {}, {}
     for i, (name, n) in enumerate(sorted(PROTOCOL_VIEWS.items())):
         w = synth.make_workload(128, n_views=n, det_w=det_w, det_h=det_h, seed=seed + i)
-        protocols[name] = serving.Protocol_(name, det_w, det_h, w.geom.matrices)
-        proj = w.projections(device=device)
-        pinned = torch.empty(proj.shape, dtype=torch.float32, pin_memory=True)
-        pinned.copy_(proj)
-        host[name] = pinned
-        del proj
+        protocols[name] = serving.Protocol_(name, det_w, det_h, w.geom.matrices, w.geom.sdd, w.geom.pitch,
+                                            w.geom.principal)
+        kinds = [(name, dict())] + ([(name + "/raw", dict(weighted=False, filtered=False))] if raw else [])
+        for key, kw in kinds:
+            proj = synth.make_projections(w.geom, w.phantom, device=device, **kw)
+            pinned = torch.empty(proj.shape, dtype=torch.float32, pin_memory=True)
+            pinned.copy_(proj)
+            host[key] = pinned
+            del proj
     torch.cuda.synchronize()
     return protocols, host
 
@@ -71,12 +75,12 @@ def _gups(L: int, mode: str) -> float:
 
 
 def run_mode(mode: str, protocols, host, *, n_requests=200, load=0.7, views_per_s=2000.0, seed=2024,
-             budget_gb=200.0, max_active=32, use_graphs=True, log=print) -> dict:
+             budget_gb=200.0, max_active=32, use_graphs=True, raw=False, log=print) -> dict:
     import torch
     svc = expected_service_s(mode)
     rate = load / svc
     reqs = serving.poisson_requests(n_requests, rate, PROTOCOL_VIEWS, seed=seed, L_choices=L_CHOICES,
-                                    L_weights=L_WEIGHTS, mode=mode, views_per_s=views_per_s)
+                                    L_weights=L_WEIGHTS, mode=mode, views_per_s=views_per_s, raw=raw)
     ex = serving.GpuExecutor(protocols, host, use_graphs=use_graphs)
     sch = serving.Scheduler(ex, int(budget_gb * (1 << 30)), max_active=max_active)
     torch.cuda.synchronize()
@@ -89,7 +93,7 @@ def run_mode(mode: str, protocols, host, *, n_requests=200, load=0.7, views_per_
     for _, ev, _ in sch.log:
         live += {"admit": 1, "done": -1, "timeout": -1}.get(ev, 0)
         peak = max(peak, live)
-    out.update({"mode": mode, "arrival_rate_hz": rate, "target_load": load, "expected_service_s": svc,
+    out.update({"mode": mode, "raw_ingest": raw, "arrival_rate_hz": rate, "target_load": load, "expected_service_s": svc,
                 "views_per_s": views_per_s, "graph_captures": ex.captures, "graph_launches": ex.graph_launches,
                 "peak_concurrent_requests": peak, "offered_updates": sum(r.updates for r in reqs),
                 "span_s": reqs[-1].arrival})
@@ -106,12 +110,14 @@ def main(argv=None):
     ap.add_argument("--load", type=float, default=0.7)
     ap.add_argument("--views-per-s", type=float, default=2000.0)
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--raw", action="store_true", help="requests send raw line integrals (filtered on the device)")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
-    protocols, host = build_protocols(dev)
+    protocols, host = build_protocols(dev, raw=args.raw)
     results = {m: run_mode(m, protocols, host, n_requests=args.requests, load=args.load,
-                           views_per_s=args.views_per_s, use_graphs=not args.no_graphs) for m in args.mode}
+                           views_per_s=args.views_per_s, use_graphs=not args.no_graphs, raw=args.raw)
+               for m in args.mode}
     if args.out:
         with open(args.out, "w") as f:
             json.dump(results, f, indent=1)

@@ -13,9 +13,10 @@ scheduler keeps the GPU busy with many requests at once:
 * every admitted request has its own CUDA stream, so chunks of different
   requests overlap on the device, and its volume stays resident in HBM;
 * each chunk pass (staging copies + the backprojection kernel, plus the FP16
-  conversion in FP16 mode) is replayed from a CUDA graph captured once per
-  slot and chunk index; slots are reused by later requests of the same shape,
-  so graphs are captured once and replayed many times;
+  conversion in FP16 mode, plus the cosine weight and ramp filter when the
+  request sends raw line integrals) is replayed from a CUDA graph captured
+  once per slot and chunk index; slots are reused by later requests of the
+  same shape, so graphs are captured once and replayed many times;
 * deadlines are enforced on the host (a request that is not complete in time
   is reported as a timeout); no device code waits on anything.
 
@@ -40,11 +41,16 @@ import numpy as np
 
 @dataclass
 class Protocol_:
-    """A calibrated scan protocol: detector size and one 3x4 matrix per view."""
+    """A calibrated scan protocol: detector size and one 3x4 matrix per view; for requests that send
+    raw line integrals, the filter geometry (source-detector distance and pixel pitch in mm, one
+    principal point (u0, v0) per view)."""
     name: str
     det_w: int
     det_h: int
     matrices: np.ndarray          # (n_views, 3, 4) float64
+    sdd: float | None = None
+    pitch: float | None = None
+    principal: np.ndarray | None = None   # (n_views, 2)
 
 
 @dataclass
@@ -60,6 +66,7 @@ class Request:
     deadline: float | None = None  # seconds from arrival; None = no deadline
     origin: tuple = None
     spacing: tuple = None
+    raw: bool = False              # chunks are raw line integrals: weighted and filtered on the device
 
     @property
     def n_chunks(self) -> int:
@@ -167,9 +174,10 @@ class Scheduler:
                         continue
                 try:
                     h = self.ex.open(r)
-                except MemoryError as e:
+                except (MemoryError, ValueError) as e:       # allocation failed, or the request is unservable
                     waiting.remove(r)
-                    results[r.rid].status, results[r.rid].message = "error", f"allocation failed: {e}"
+                    what = "allocation failed" if isinstance(e, MemoryError) else "cannot serve"
+                    results[r.rid].status, results[r.rid].message = "error", f"{what}: {e}"
                     self.log.append((now, "error", r.rid))
                     continue
                 waiting.remove(r)
@@ -239,7 +247,7 @@ def summarize(results: list[Result], requests: list[Request], wall_s: float) -> 
 def poisson_requests(n: int, rate_hz: float, protocols: dict[str, int], *, seed: int = 0,
                      L_choices=(128, 256, 512, 1024), L_weights=(0.4, 0.3, 0.2, 0.1), mode: str = "f32",
                      chunk_views: int = 16, views_per_s: float = 2000.0, deadline: float | None = None,
-                     origin_spacing: Callable[[int], tuple] | None = None) -> list[Request]:
+                     origin_spacing: Callable[[int], tuple] | None = None, raw: bool = False) -> list[Request]:
     """Seeded Poisson arrivals with mixed L and protocols (protocol name -> view count)."""
     rng = np.random.default_rng(seed)
     t = 0.0
@@ -251,7 +259,7 @@ def poisson_requests(n: int, rate_hz: float, protocols: dict[str, int], *, seed:
         name = names[int(rng.integers(len(names)))]
         o, s = origin_spacing(L) if origin_spacing else (None, None)
         out.append(Request(i, L, name, protocols[name], t, mode, chunk_views, chunk_views / views_per_s,
-                           deadline, o, s))
+                           deadline, o, s, raw))
     return out
 
 
@@ -306,7 +314,7 @@ class GpuExecutor:
     def _key(self, r: Request) -> tuple:
         o = tuple(r.origin) if r.origin is not None else None
         s = tuple(r.spacing) if r.spacing is not None else None
-        return (r.L, r.protocol, r.n_views, r.mode, r.chunk_views, o, s)
+        return (r.L, r.protocol, r.n_views, r.mode, r.chunk_views, o, s, r.raw)
 
     def footprint(self, r: Request) -> int:
         p = self.protocols[r.protocol]
@@ -357,6 +365,11 @@ class GpuExecutor:
         code = rct.RCT_PROJ_F16 if r.mode == "f16" else rct.RCT_PROJ_F32
         bp.set_precision(code, rct.RCT_INTERP_SOFT)
         bp.set_tuning(**self.tuning_fn(r.L, r.mode))
+        if r.raw:
+            if p.sdd is None or p.pitch is None or p.principal is None:
+                bp.close()
+                raise ValueError(f"protocol {p.name} has no filter geometry for raw projections")
+            bp.set_filter(p.sdd, p.pitch, p.principal[:r.n_views])
         rct.rct_prepare(bp.ctx, False)
         stream = torch.cuda.Stream(device=self.device)
         d_chunk = torch.empty((r.chunk_views, p.det_h, p.det_w), dtype=torch.float32, device=self.device)
@@ -381,7 +394,13 @@ class GpuExecutor:
         a, b = r.chunk_range(c)
         n = b - a
         src = slot.d_chunk
-        if slot.d_half is not None:
+        if r.raw:
+            # cosine weight + ramp filter; FP16 mode writes the narrowed result directly
+            dst, code = ((slot.d_half, rct.RCT_PROJ_F16) if slot.d_half is not None
+                         else (slot.d_chunk, rct.RCT_PROJ_F32))
+            rct.rct_filter_projections(slot.bp.ctx, slot.d_chunk, dst, code, a, n, slot.stream)
+            src = dst
+        elif slot.d_half is not None:
             rct.rct_convert_projections(slot.d_chunk, slot.d_half, n * slot.d_chunk[0].numel(),
                                         rct.RCT_PROJ_F16, slot.stream)
             src = slot.d_half
@@ -392,7 +411,7 @@ class GpuExecutor:
         slot = self.free_slots[key].pop() if self.free_slots[key] else self._new_slot(r)
         if not self.use_graphs:
             slot.bp.reset(slot.stream)
-        return _Handle(r, slot, self.host[r.protocol])
+        return _Handle(r, slot, self.host[r.protocol + "/raw" if r.raw else r.protocol])
 
     def submit_chunk(self, h: _Handle, c: int) -> None:
         torch = self.torch

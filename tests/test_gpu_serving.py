@@ -17,17 +17,19 @@ def setup(cuda_device):
     protos, host, works = {}, {}, {}
     for name, n, seed in [("pA", 24, 51), ("pB", 40, 52)]:
         w = synth.make_workload(32, n_views=n, det_w=W, det_h=H, seed=seed)
-        protos[name] = serving.Protocol_(name, W, H, w.geom.matrices)
+        protos[name] = serving.Protocol_(name, W, H, w.geom.matrices, w.geom.sdd, w.geom.pitch, w.geom.principal)
         p = w.projections(device=cuda_device)
         host[name] = p.cpu().pin_memory()
+        raw = synth.make_projections(w.geom, w.phantom, device=cuda_device, weighted=False, filtered=False)
+        host[name + "/raw"] = raw.cpu().pin_memory()
         works[name] = w
     return protos, host, works
 
 
-def _req(rid, L, proto, n, arrival, mode="f32", interval=0.0):
+def _req(rid, L, proto, n, arrival, mode="f32", interval=0.0, raw=False):
     sp = 256.0 / L
     return serving.Request(rid, L, proto, n, arrival, mode, chunk_views=16, chunk_interval=interval,
-                           origin=(-(L - 1) / 2 * sp,) * 3, spacing=(sp,) * 3)
+                           origin=(-(L - 1) / 2 * sp,) * 3, spacing=(sp,) * 3, raw=raw)
 
 
 def _serve(protos, host, reqs, graphs=True):
@@ -76,3 +78,35 @@ def test_slots_and_graphs_are_reused_across_requests(setup):
     assert [r.status for r in res] == ["ok", "ok"]
     assert captures == reqs[0].n_chunks and launches == 2 * reqs[0].n_chunks
     assert torch.equal(res[0].volume, res[1].volume)
+
+
+@pytest.mark.parametrize("mode", ["f32", "f16"])
+def test_raw_ingest_filters_on_the_device(setup, mode, cuda_device):
+    """A request that sends raw line integrals gets the same volume, bit for bit, as one that sends
+    the device filter's output (computed up front through rct_filter_projections), alone and in a mix."""
+    from paper_1401_7494_gb300 import rct
+    protos, host, works = setup
+    p, w = protos["pB"], works["pB"]
+    raw_dev = host["pB/raw"].to(cuda_device)
+    filt = torch.empty_like(raw_dev)
+    with rct.Backprojector(8, W, H, w.n_views) as bp:
+        bp.set_filter(p.sdd, p.pitch, p.principal)
+        bp.filter(raw_dev, filt)
+        torch.cuda.synchronize()
+    host2 = dict(host, pF=filt.cpu().pin_memory())
+    protos2 = dict(protos, pF=serving.Protocol_("pF", W, H, p.matrices, p.sdd, p.pitch, p.principal))
+    pre, _ = _serve(protos2, host2, [_req(0, 37, "pF", 40, 0.0, mode)])
+    mix = [_req(0, 37, "pB", 40, 0.001, mode, interval=0.001, raw=True),
+           _req(1, 24, "pA", 24, 0.0, mode, interval=0.0007),
+           _req(2, 48, "pB", 40, 0.0005, mode, interval=0.0007, raw=True)]
+    res, _ = _serve(protos2, host2, mix)
+    assert all(r.status == "ok" for r in res)
+    assert torch.equal(res[0].volume, pre[0].volume)
+
+
+def test_raw_ingest_needs_filter_geometry(setup):
+    protos, host, _ = setup
+    bare = dict(protos, pX=serving.Protocol_("pX", W, H, protos["pA"].matrices))
+    host2 = dict(host, **{"pX/raw": host["pA/raw"]})
+    res, _ = _serve(bare, host2, [_req(0, 24, "pX", 24, 0.0, raw=True)])
+    assert res[0].status == "error"
