@@ -255,8 +255,8 @@ __device__ __forceinline__ void block_frame(const ViewGeo *vg, float bX, float b
 // always takes the global frame (the texture unit needs absolute coordinates).
 // TRUNC: the cell index of Listing 1's (int) cast, which truncates toward zero, instead of floor
 // (RabbitCT compatibility; plain loads only).
-template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = false>
-__global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParams p) {
+template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC>
+__device__ __forceinline__ void bp_body(const BpParams &p) {
     static_assert(!FRAME || G == G_SOFT, "block frames are for the software gathers");
     static_assert(!TRUNC || (G == G_SOFT && ROUTE == ROUTE_LDG && !FRAME), "truncation: global frame, plain loads");
     const int L = p.L;
@@ -432,11 +432,31 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
 }
 
 template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = false>
+__global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParams p) {
+    bp_body<G, DT, XV, R, ROUTE, FRAME, TRUNC>(p);
+}
+
+// Block-frame kernels keep the frame's rows and shift in per-thread registers through the z-run;
+// capped at RCT_FRAME_MAXREG registers they keep more warps resident, which measured faster (the
+// global-frame kernels measured slower under any cap).
+#ifndef RCT_FRAME_MAXREG
+#define RCT_FRAME_MAXREG 48
+#endif
+template <int DT, int XV, int R, int ROUTE>
+__global__ void __maxnreg__(RCT_FRAME_MAXREG) bp_kernel_frame(const __grid_constant__ BpParams p) {
+    bp_body<G_SOFT, DT, XV, R, ROUTE, true, false>(p);
+}
+
+template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = false>
 cudaError_t launch_one(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     if (FRAME && !p.geo) return cudaErrorInvalidValue;
     const int gx = (p.L / XV + c.bx - 1) / c.bx;
     const dim3 grid(gx, (p.L + c.by - 1) / c.by, (p.L + R - 1) / R);
-    bp_kernel<G, DT, XV, R, ROUTE, FRAME, TRUNC><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
+    if constexpr (FRAME) {
+        bp_kernel_frame<DT, XV, R, ROUTE><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
+    } else {
+        bp_kernel<G, DT, XV, R, ROUTE, FRAME, TRUNC><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 
