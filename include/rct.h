@@ -251,6 +251,17 @@ RCT_API rct_status rct_backproject(rct_ctx *ctx, const void *d_proj, int first_v
  */
 RCT_API rct_status rct_backproject_host(rct_ctx *ctx, const void *h_proj, int first_view, int n, void *stream);
 
+/*
+ * rct_backproject_host followed by rct_read_volume(ctx, dst, stream), with the read-back overlapped:
+ * the last pass of the call runs as z-slabs and each slab's planes are copied to dst (host or
+ * device, L^3 floats, z-major, x fastest) as soon as that slab is done, on the context's copy
+ * stream; `stream` waits for the last copy, so dst is complete once `stream` reaches the call.
+ * Same arguments and errors as the two calls (RCT_EINVAL for a null dst); the volume stays in the
+ * context as well.  The result is bit for bit that of the two separate calls.
+ */
+RCT_API rct_status rct_backproject_host_read(rct_ctx *ctx, const void *h_proj, int first_view, int n, float *dst,
+                                             void *stream);
+
 /* Copy the volume (L^3 floats) to dst, host or device memory.  Enqueued on stream. */
 RCT_API rct_status rct_read_volume(rct_ctx *ctx, float *dst, void *stream);
 

@@ -43,6 +43,7 @@ rct_status cuda_fail(cudaError_t e, const char *what) {
 size_t dtype_size(int dt) { return dt == DT_F32 ? 4 : 2; }
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kReadSlabs = 8;   // z-slabs of the last pass when the read-back overlaps it
 
 // One staging slot: a 2D CUDA array that holds one view for texture sampling.
 struct Slot {
@@ -128,6 +129,7 @@ struct rct_ctx {
     size_t widen_elems = 0;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_filled[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> ev_slab;   // read-back overlap: one per z-slab of the last pass, plus one for the end
     cudaEvent_t ev_free[2] = {nullptr, nullptr};
 
     int64_t launches = 0;
@@ -561,6 +563,8 @@ void rct_destroy(rct_ctx *c) {
     if (c->lin_stage) cudaFree(c->lin_stage);
     if (c->quad_buf) cudaFree(c->quad_buf);
     if (c->geo_dev) cudaFree(c->geo_dev);
+    for (cudaEvent_t e : c->ev_slab) cudaEventDestroy(e);
+    c->ev_slab.clear();
     if (c->filt_twiddle) cudaFree(c->filt_twiddle);
     if (c->filt_spectrum) cudaFree(c->filt_spectrum);
     if (c->filt_principal) cudaFree(c->filt_principal);
@@ -866,11 +870,14 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
     return RCT_OK;
 }
 
-rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, int n, void *stream) {
-    rct_status st = check_ctx(c);
-    if (st) return st;
-    if ((st = validate_range(c, h_proj, first_view, n))) return st;
-    if (n == 0) return RCT_OK;
+namespace {
+
+// The host-input path (see rct_backproject_host).  With read_dst, the last pass runs as z-slabs and
+// each slab's planes are copied to read_dst on the copy stream as soon as that slab is done, so the
+// read-back overlaps the rest of the pass; `stream` then waits for the last copy.
+rct_status backproject_host_impl(rct_ctx *c, const void *h_proj, int first_view, int n, void *stream,
+                                 float *read_dst) {
+    rct_status st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int kind = kernel_kind(c);
     const int K = c->tune.views_per_pass;
@@ -920,12 +927,60 @@ rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, 
         }
         RCT_CUDA(cudaEventRecord(c->ev_filled[g], c->copy_stream), "cudaEventRecord");
         RCT_CUDA(cudaStreamWaitEvent(s, c->ev_filled[g], 0), "cudaStreamWaitEvent");
-        cudaError_t e = launch(c, lc, p, s);
-        if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
+        if (read_dst && b + kb >= n) {
+            // last pass: z-slabs of a whole number of z-runs, each copied out when it is done
+            const int R = c->tune.zrun;
+            const int slab = ((c->L + kReadSlabs - 1) / kReadSlabs + R - 1) / R * R;
+            const size_t plane = (size_t)c->L * c->L;
+            int i = 0;
+            for (int z = 0; z < c->L; z += slab, ++i) {
+                p.z_base = z;
+                p.z_count = std::min(slab, c->L - z);
+                cudaError_t e = launch(c, lc, p, s);
+                if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
+                RCT_CUDA(cudaEventRecord(c->ev_slab[i], s), "cudaEventRecord");
+                RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_slab[i], 0), "cudaStreamWaitEvent");
+                RCT_CUDA(cudaMemcpyAsync(read_dst + z * plane, c->vol + z * plane, sizeof(float) * plane * p.z_count,
+                                         cudaMemcpyDefault, c->copy_stream),
+                         "cudaMemcpyAsync(volume slab)");
+            }
+            p.z_base = p.z_count = 0;
+            RCT_CUDA(cudaEventRecord(c->ev_slab[i], c->copy_stream), "cudaEventRecord");
+            RCT_CUDA(cudaStreamWaitEvent(s, c->ev_slab[i], 0), "cudaStreamWaitEvent");
+        } else {
+            cudaError_t e = launch(c, lc, p, s);
+            if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
+        }
         c->vol_zero_pending = false;
         RCT_CUDA(cudaEventRecord(c->ev_free[g], s), "cudaEventRecord");
     }
     return RCT_OK;
+}
+
+}  // namespace
+
+rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, int n, void *stream) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if ((st = validate_range(c, h_proj, first_view, n))) return st;
+    if (n == 0) return RCT_OK;
+    return backproject_host_impl(c, h_proj, first_view, n, stream, nullptr);
+}
+
+rct_status rct_backproject_host_read(rct_ctx *c, const void *h_proj, int first_view, int n, float *dst,
+                                     void *stream) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if ((st = validate_range(c, h_proj, first_view, n))) return st;
+    if (!dst) return fail(RCT_EINVAL, "null destination");
+    if (n == 0) return rct_read_volume(c, dst, stream);
+    if ((st = ensure_copy_machinery(c))) return st;
+    while (c->ev_slab.size() < kReadSlabs + 1) {
+        cudaEvent_t e;
+        RCT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        c->ev_slab.push_back(e);
+    }
+    return backproject_host_impl(c, h_proj, first_view, n, stream, dst);
 }
 
 rct_status rct_read_volume(rct_ctx *c, float *dst, void *stream) {

@@ -262,7 +262,7 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
     const int L = p.L;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * XV;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z0 = blockIdx.z * R;
+    const int z0 = p.z_base + blockIdx.z * R;
     // the block's first voxel (centred coordinates, exact) and this thread's offset from it
     const float bX = static_cast<float>(blockIdx.x * blockDim.x * XV) - p.cen;
     const float bY = static_cast<float>(blockIdx.y * blockDim.y) - p.cen;
@@ -451,7 +451,8 @@ template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = fals
 cudaError_t launch_one(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     if (FRAME && !p.geo) return cudaErrorInvalidValue;
     const int gx = (p.L / XV + c.bx - 1) / c.bx;
-    const dim3 grid(gx, (p.L + c.by - 1) / c.by, (p.L + R - 1) / R);
+    const int zc = p.z_count > 0 ? p.z_count : p.L;
+    const dim3 grid(gx, (p.L + c.by - 1) / c.by, (zc + R - 1) / R);
     if constexpr (FRAME) {
         bp_kernel_frame<DT, XV, R, ROUTE><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
     } else {

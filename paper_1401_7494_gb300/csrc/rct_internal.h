@@ -68,6 +68,8 @@ struct BpParams {
     int quad;        // G_SOFT load route: 0 = linear image, 1 = staged quads, 2 = staged pairs
     const ViewGeo *geo;  // G_SOFT: the context's per-view geometry for block frames (null: global frame)
     int first_view;      // view index of view[0] in geo
+    int z_base;          // first z plane of this launch (0: the whole volume)
+    int z_count;         // z planes from z_base (0: all L); a multiple of the z-run unless it ends at L
     ViewParams view[KMAX];
 };
 

@@ -66,6 +66,7 @@ SIGNATURES = {
     "rct_reset_volume": (_I, [_P, _P]),
     "rct_backproject": (_I, [_P, _P, _I, _I, _P]),
     "rct_backproject_host": (_I, [_P, _P, _I, _I, _P]),
+    "rct_backproject_host_read": (_I, [_P, _P, _I, _I, _P, _P]),
     "rct_read_volume": (_I, [_P, _P, _P]),
     "rct_write_volume": (_I, [_P, _P, _P]),
     "rct_volume_device_ptr": (_P, [_P]),
@@ -241,6 +242,10 @@ def rct_backproject(ctx, d_proj, first_view: int, n: int, stream=None) -> None:
 
 def rct_backproject_host(ctx, h_proj, first_view: int, n: int, stream=None) -> None:
     _check(lib().rct_backproject_host(ctx, _addr(h_proj), first_view, n, _stream(stream)))
+
+
+def rct_backproject_host_read(ctx, h_proj, first_view: int, n: int, dst, stream=None) -> None:
+    _check(lib().rct_backproject_host_read(ctx, _addr(h_proj), first_view, n, _addr(dst), _stream(stream)))
 
 
 def rct_read_volume(ctx, dst, stream=None) -> None:
@@ -422,6 +427,11 @@ class Backprojector:
         if n is None:
             n = int(h_proj.shape[0])
         rct_backproject_host(self.ctx, h_proj, first_view, n, stream)
+
+    def backproject_host_read(self, h_proj, dst, first_view=0, n=None, stream=None):
+        if n is None:
+            n = int(h_proj.shape[0])
+        rct_backproject_host_read(self.ctx, h_proj, first_view, n, dst, stream)
 
     def read_volume(self, dst, stream=None):
         rct_read_volume(self.ctx, dst, stream)

@@ -358,3 +358,57 @@ def test_index_rule_argument_errors(cuda_device):
         with pytest.raises(rct.RctError) as e:
             rct.rct_set_geometry_rabbitct(bp.ctx, np.zeros(12 * 4, np.float32), 0.0, -1.0)   # spacing <= 0
         assert e.value.status == rct.RCT_EINVAL
+
+
+@pytest.mark.parametrize("case", ["L37", "L64"])
+@pytest.mark.parametrize("tuning,frame", [(dict(zrun=8, views_per_pass=16), rct.RCT_FRAME_GLOBAL),
+                                          (dict(zrun=4, views_per_pass=7, gather=rct.RCT_GATHER_PAIR), rct.RCT_FRAME_GLOBAL),
+                                          (dict(zrun=2, xvec=1, views_per_pass=32), rct.RCT_FRAME_BLOCK),
+                                          (dict(zrun=16, xvec=1, gather=rct.RCT_GATHER_TLD4), rct.RCT_FRAME_GLOBAL)])
+def test_overlapped_read_back_is_bitwise_the_separate_calls(small_cases, cuda_device, case, tuning, frame):
+    """rct_backproject_host_read (last pass in z-slabs, each copied out when done) against
+    rct_backproject_host + rct_read_volume: same bits, to pinned host memory and to device memory, also
+    after an earlier call has filled part of the volume."""
+    w, proj, _ = small_cases[case]
+    pinned = proj.cpu().pin_memory()
+    stream = torch.cuda.current_stream()
+    split = w.n_views // 3
+    shape = (w.L,) * 3
+    outs = {}
+    for mode in ("separate", "host", "device"):
+        with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+            bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_frame(frame).set_tuning(**tuning)
+            bp.backproject_host(pinned[:split], 0, split, stream)
+            rest = pinned[split:]
+            if mode == "separate":
+                dst = torch.empty(shape, dtype=torch.float32, device=cuda_device)
+                bp.backproject_host(rest, split, w.n_views - split, stream)
+                bp.read_volume(dst, stream)
+            elif mode == "host":
+                dst = torch.empty(shape, dtype=torch.float32).pin_memory()
+                bp.backproject_host_read(rest, dst, split, w.n_views - split, stream)
+            else:
+                dst = torch.empty(shape, dtype=torch.float32, device=cuda_device)
+                bp.backproject_host_read(rest, dst, split, w.n_views - split, stream)
+            stream.synchronize()
+            outs[mode] = dst.cpu()
+    assert torch.equal(outs["host"], outs["separate"])
+    assert torch.equal(outs["device"], outs["separate"])
+
+
+def test_overlapped_read_back_edge_cases(small_cases, cuda_device):
+    w, proj, host = small_cases["L40"]
+    pinned = proj.cpu().pin_memory()
+    stream = torch.cuda.current_stream()
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
+        dst = torch.full((w.L,) * 3, 7.0).pin_memory()
+        bp.backproject_host_read(pinned[:0], dst, 0, 0, stream)           # n == 0: the (zero) volume
+        stream.synchronize()
+        assert torch.count_nonzero(dst) == 0
+        bp.backproject_host_read(pinned, dst, 0, w.n_views, stream)        # one call, whole scan
+        stream.synchronize()
+        assert_parity(dst.numpy(), oracle_volume(w, host), "overlapped read-back")
+        with pytest.raises(rct.RctError) as e:
+            rct.rct_backproject_host_read(bp.ctx, pinned, 0, 1, 0, None)
+        assert e.value.status == rct.RCT_EINVAL
