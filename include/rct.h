@@ -184,6 +184,19 @@ RCT_API rct_status rct_get_frame(const rct_ctx *ctx, int *frame);
  * (world position of voxel (x, y, z) = (O + x MM, O + y MM, O + z MM)).  It widens them to FP64
  * and calls rct_set_geometry, with the same errors.
  */
+/*
+ * Bounds-checking build (the library compiled with -DRCT_CHECK_BOUNDS; the Python binding builds and
+ * loads it when RCT_BUILD_VARIANT=check): every computed index of a staged image, of a plain-load
+ * tap and of the volume is checked before the access, a violation is counted and the access
+ * skipped.  rct_debug_bound_violations synchronises the device and returns the context's count;
+ * RCT_ENOTSUP from the normal build.
+ */
+RCT_API rct_status rct_debug_bound_violations(rct_ctx *ctx, unsigned long long *count);
+/* Checking build only: compare staged-image indices against at most staged_elems elements (0 restores
+ * the real size), so that in-bounds accesses past that limit are counted and skipped -- a control
+ * that the checks are live.  No access leaves its buffer.  RCT_ENOTSUP from the normal build. */
+RCT_API rct_status rct_debug_lower_bound_limit(rct_ctx *ctx, long long staged_elems);
+
 RCT_API rct_status rct_set_index_rule(rct_ctx *ctx, int rule);
 RCT_API rct_status rct_get_index_rule(const rct_ctx *ctx, int *rule);
 RCT_API rct_status rct_set_geometry_rabbitct(rct_ctx *ctx, const float *matrices, float O, float MM);

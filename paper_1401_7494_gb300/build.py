@@ -15,7 +15,12 @@ from pathlib import Path
 
 PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
-BUILD = PKG / "_build"
+# RCT_BUILD_VARIANT=check builds (and the binding loads) the bounds-checking library in its own folder
+VARIANTS = {"": ("_build", []), "check": ("_build_check", ["-DRCT_CHECK_BOUNDS"])}
+VARIANT = os.environ.get("RCT_BUILD_VARIANT", "")
+if VARIANT not in VARIANTS:
+    raise RuntimeError(f"RCT_BUILD_VARIANT={VARIANT!r}: expected one of {sorted(VARIANTS)}")
+BUILD = PKG / VARIANTS[VARIANT][0]
 LIB = BUILD / "librct.so"
 INCLUDE = PKG.parent / "include"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -53,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> Path:
 
     def compile_one(src: Path) -> Path:
         obj = BUILD / (src.stem + ".o")
-        cmd = [exe, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", str(src), "-o", str(obj)]
+        cmd = [exe, *ARCH, *NVCC_FLAGS, *VARIANTS[VARIANT][1], *extra_flags, "-c", str(src), "-o", str(obj)]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src.name}:\n{r.stderr}")

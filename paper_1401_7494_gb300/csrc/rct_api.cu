@@ -130,6 +130,8 @@ struct rct_ctx {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_filled[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> ev_slab;   // read-back overlap: one per z-slab of the last pass, plus one for the end
+    unsigned long long *viol_dev = nullptr;   // bounds-checking build: violation counter
+    long long debug_qelems = 0;               // bounds-checking build: lowered staged-image limit (0: none)
     cudaEvent_t ev_free[2] = {nullptr, nullptr};
 
     int64_t launches = 0;
@@ -335,6 +337,11 @@ void init_params(const rct_ctx *c, BpParams *p) {
     p->tex_zrun = tex_zrun_of(c);
     p->quad = load_layout(c);
     p->geo = (c->frame == RCT_FRAME_BLOCK) ? c->geo_dev : nullptr;
+    p->viol = c->viol_dev;
+    if (load_layout(c) != 0)
+        p->qelems = static_cast<long long>(layout_bytes(c) /
+                                           ((load_layout(c) == 2 ? 2 : 4) * dtype_size(c->dtype)));
+    if (c->debug_qelems > 0) p->qelems = std::min(p->qelems, c->debug_qelems);
 }
 
 // FP32 view parameters for one view and kernel kind, from the FP64 fold.
@@ -549,6 +556,16 @@ rct_ctx *rct_create(int L, int det_w, int det_h, int n_views) {
     }
     c->fold.assign(12 * (size_t)n_views, 0.0);
     c->shift.assign(2 * (size_t)n_views, 0);
+#ifdef RCT_CHECK_BOUNDS
+    if (cudaMalloc(&c->viol_dev, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->viol_dev, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        fail(RCT_ENOMEM, "rct_create: violation counter allocation failed");
+        cudaFree(c->vol);
+        if (c->viol_dev) cudaFree(c->viol_dev);
+        delete c;
+        return nullptr;
+    }
+#endif
     return c;
 }
 
@@ -565,6 +582,7 @@ void rct_destroy(rct_ctx *c) {
     if (c->geo_dev) cudaFree(c->geo_dev);
     for (cudaEvent_t e : c->ev_slab) cudaEventDestroy(e);
     c->ev_slab.clear();
+    if (c->viol_dev) cudaFree(c->viol_dev);
     if (c->filt_twiddle) cudaFree(c->filt_twiddle);
     if (c->filt_spectrum) cudaFree(c->filt_spectrum);
     if (c->filt_principal) cudaFree(c->filt_principal);
@@ -722,6 +740,35 @@ rct_status rct_filter_projections(rct_ctx *c, const float *d_raw, void *d_out, i
     cudaError_t e = launch_ramp_filter(f, d_raw, d_out, out_dtype, n, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "ramp filter launch");
     return RCT_OK;
+}
+
+rct_status rct_debug_bound_violations(rct_ctx *c, unsigned long long *count) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if (!count) return fail(RCT_EINVAL, "null pointer");
+#ifdef RCT_CHECK_BOUNDS
+    if (!c->viol_dev) {
+        *count = 0;
+        return RCT_OK;
+    }
+    RCT_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    RCT_CUDA(cudaMemcpy(count, c->viol_dev, sizeof *count, cudaMemcpyDeviceToHost), "cudaMemcpy");
+    return RCT_OK;
+#else
+    return fail(RCT_ENOTSUP, "this library was built without bounds checks");
+#endif
+}
+
+rct_status rct_debug_lower_bound_limit(rct_ctx *c, long long staged_elems) {
+    rct_status st = check_ctx(c);
+    if (st) return st;
+    if (staged_elems < 0) return fail(RCT_EINVAL, "negative limit");
+#ifdef RCT_CHECK_BOUNDS
+    c->debug_qelems = staged_elems;
+    return RCT_OK;
+#else
+    return fail(RCT_ENOTSUP, "this library was built without bounds checks");
+#endif
 }
 
 rct_status rct_set_index_rule(rct_ctx *c, int rule) {

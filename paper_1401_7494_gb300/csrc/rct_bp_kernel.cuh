@@ -79,6 +79,16 @@ __device__ __forceinline__ float load_px(const void *img, ptrdiff_t off) {
 }
 
 // Per-view constants the inner loop needs, hoisted out of the z-run.
+// Bounds-checking build (-DRCT_CHECK_BOUNDS): every computed index of a staged image, of a plain-load
+// tap and of the volume is checked against its buffer before the access; a violation is counted on
+// the device (BpParams::viol) and the access is skipped -- never a trap.
+#ifdef RCT_CHECK_BOUNDS
+__device__ __forceinline__ bool rct_in_bounds(bool ok, unsigned long long *viol) {
+    if (!ok && viol) atomicAdd(viol, 1ull);
+    return ok;
+}
+#endif
+
 struct ViewConsts {
     float2 m_z;      // (m[2], m[6]): step of (u', v') per z voxel
     float w_z;       // m[10]
@@ -88,6 +98,10 @@ struct ViewConsts {
     cudaTextureObject_t tex;
     const void *img;
     const void *quad;
+#ifdef RCT_CHECK_BOUNDS
+    long long qelems;
+    unsigned long long *viol;
+#endif
 };
 
 // Route of the load part of a z-run (G_SOFT only).
@@ -142,6 +156,9 @@ __device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 t, f
                     static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
     const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 1) + static_cast<unsigned>(ix) : 0u;
     w2 = on ? w2 : 0.0f;
+#ifdef RCT_CHECK_BOUNDS
+    if (!rct_in_bounds(static_cast<long long>(e) < c.qelems, c.viol)) return;
+#endif
     float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
     if constexpr (DT == DT_F32) {
         const float4 v = __ldg(static_cast<const float4 *>(c.quad) + e);
@@ -173,6 +190,9 @@ __device__ __forceinline__ void accumulate_pair(const ViewConsts &c, float2 t, f
                     static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
     const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 2) + static_cast<unsigned>(ix) : 0u;
     w2 = on ? w2 : 0.0f;
+#ifdef RCT_CHECK_BOUNDS
+    if (!rct_in_bounds(static_cast<long long>(e) + 1 < c.qelems, c.viol)) return;
+#endif
     float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
     if constexpr (DT == DT_F32) {
         const float2 *pp = static_cast<const float2 *>(c.quad) + e;
@@ -203,6 +223,15 @@ __device__ __forceinline__ void accumulate_ldg(const ViewConsts &c, float2 t, fl
     const bool y0 = static_cast<unsigned>(j0) < static_cast<unsigned>(H);
     const bool y1 = static_cast<unsigned>(j0 + 1) < static_cast<unsigned>(H);
     const ptrdiff_t o = static_cast<ptrdiff_t>(j0) * W + i0;
+#ifdef RCT_CHECK_BOUNDS
+    {
+        const ptrdiff_t px = static_cast<ptrdiff_t>(W) * H;
+        const auto in = [px](ptrdiff_t q) { return q >= 0 && q < px; };
+        if (!rct_in_bounds(!(y0 && x0) || in(o), c.viol) || !rct_in_bounds(!(y0 && x1) || in(o + 1), c.viol) ||
+            !rct_in_bounds(!(y1 && x0) || in(o + W), c.viol) || !rct_in_bounds(!(y1 && x1) || in(o + W + 1), c.viol))
+            return;
+    }
+#endif
     const float a = (y0 && x0) ? load_px<DT>(c.img, o) : 0.0f;
     const float b = (y0 && x1) ? load_px<DT>(c.img, o + 1) : 0.0f;
     const float cc = (y1 && x0) ? load_px<DT>(c.img, o + W) : 0.0f;
@@ -296,7 +325,13 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
     float acc[R][XV];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const bool live = p.accumulate && (z0 + r < L);
+        bool live = p.accumulate && (z0 + r < L);
+#ifdef RCT_CHECK_BOUNDS
+        {
+            const long long at = static_cast<long long>(z0 + r) * L * L + static_cast<long long>(y) * L + x0;
+            if (live) live = rct_in_bounds(at >= 0 && at + XV <= static_cast<long long>(L) * L * L, p.viol);
+        }
+#endif
         if constexpr (XV == 4) {
             float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
             if (live) t = __ldcs(reinterpret_cast<const float4 *>(vb + r * plane));
@@ -324,6 +359,10 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
         c.tex = static_cast<cudaTextureObject_t>(v.tex);
         c.img = v.img;
         c.quad = v.quad;
+#ifdef RCT_CHECK_BOUNDS
+        c.qelems = p.qelems;
+        c.viol = p.viol;
+#endif
         float2 m_x, buv;
         float bw;
         if constexpr (FRAME) {
@@ -421,6 +460,12 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (z0 + r >= L) break;
+#ifdef RCT_CHECK_BOUNDS
+        {
+            const long long at = static_cast<long long>(z0 + r) * L * L + static_cast<long long>(y) * L + x0;
+            if (!rct_in_bounds(at >= 0 && at + XV <= static_cast<long long>(L) * L * L, p.viol)) continue;
+        }
+#endif
         if constexpr (XV == 4) {
             __stcs(reinterpret_cast<float4 *>(vb + r * plane), make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]));
         } else if constexpr (XV == 2) {

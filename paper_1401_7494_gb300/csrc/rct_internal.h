@@ -70,6 +70,8 @@ struct BpParams {
     int first_view;      // view index of view[0] in geo
     int z_base;          // first z plane of this launch (0: the whole volume)
     int z_count;         // z planes from z_base (0: all L); a multiple of the z-run unless it ends at L
+    long long qelems;    // elements of one staged quad / pair image (bounds-checking build only)
+    unsigned long long *viol;  // bounds-checking build: violation counter on the device (null: not counted)
     ViewParams view[KMAX];
 };
 

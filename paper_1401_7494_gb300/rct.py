@@ -57,6 +57,8 @@ SIGNATURES = {
     "rct_set_frame": (_I, [_P, _I]),
     "rct_get_frame": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "rct_set_index_rule": (_I, [_P, _I]),
+    "rct_debug_bound_violations": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "rct_debug_lower_bound_limit": (_I, [_P, ctypes.c_longlong]),
     "rct_set_filter": (_I, [_P, ctypes.c_double, ctypes.c_double, _D3]),
     "rct_filter_projections": (_I, [_P, _P, _P, _I, _I, _I, _P]),
     "rct_get_index_rule": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
@@ -201,6 +203,16 @@ def rct_set_filter(ctx, sdd: float, pitch: float, principal) -> None:
 def rct_filter_projections(ctx, d_raw, d_out, out_dtype: int, first_view: int, n: int, stream=None) -> None:
     _check(lib().rct_filter_projections(ctx, _addr(d_raw), _addr(d_out), int(out_dtype), first_view, n,
                                         _stream(stream)))
+
+
+def rct_debug_bound_violations(ctx) -> int:
+    n = ctypes.c_ulonglong()
+    _check(lib().rct_debug_bound_violations(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def rct_debug_lower_bound_limit(ctx, staged_elems: int) -> None:
+    _check(lib().rct_debug_lower_bound_limit(ctx, int(staged_elems)))
 
 
 def rct_set_index_rule(ctx, rule: int) -> None:
