@@ -37,7 +37,7 @@ UNIT = "GUPS"
 # (traffic reported as null).  Source: profiles/bp_kernel_pair_f32_L512_ncu_full.md.
 TRAFFIC: dict = {
     '{"block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0, "views_per_pass": 24, "xvec": 1, "zrun": 8}':
-        786_650_112 + 482_411_776,
+        787_052_288 + 482_466_816,
 }
 
 
