@@ -206,7 +206,7 @@ def measure_variant(w, proj_dev, dtype: str, interp: str, steps: int, warmup: in
     if dtype != "f32":
         data = torch.empty(proj_dev.shape, dtype=tdt, device=proj_dev.device)
         rct.rct_convert_projections(proj_dev, data, proj_dev.numel(), codes[dtype], stream)
-    tun = tuning.lookup(w.L, dtype, interp)
+    tun = tuning.lookup(w.L, dtype, interp, frame=frame)
     out = {"tuning": tun, "frame": frame, "index_rule": "trunc" if trunc else "floor"}
     with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
         bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_precision(codes[dtype], interp_code)

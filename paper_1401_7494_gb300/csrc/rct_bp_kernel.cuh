@@ -481,15 +481,21 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
     bp_body<G, DT, XV, R, ROUTE, FRAME, TRUNC>(p);
 }
 
-// Block-frame kernels keep the frame's rows and shift in per-thread registers through the z-run;
-// capped at RCT_FRAME_MAXREG registers they keep more warps resident, which measured faster (the
-// global-frame kernels measured slower under any cap).
-#ifndef RCT_FRAME_MAXREG
-#define RCT_FRAME_MAXREG 48
+// Register caps (measured): the block-frame kernels keep the frame's rows and shift in per-thread
+// registers through the z-run, and the z-runs of 16 keep 16 partial sums; capped at
+// RCT_CAPPED_MAXREG registers both keep more warps resident and run faster, while the global-frame
+// kernels with shorter z-runs run slower under any cap.
+#ifndef RCT_CAPPED_MAXREG
+#define RCT_CAPPED_MAXREG 48
 #endif
 template <int DT, int XV, int R, int ROUTE>
-__global__ void __maxnreg__(RCT_FRAME_MAXREG) bp_kernel_frame(const __grid_constant__ BpParams p) {
+__global__ void __maxnreg__(RCT_CAPPED_MAXREG) bp_kernel_frame(const __grid_constant__ BpParams p) {
     bp_body<G_SOFT, DT, XV, R, ROUTE, true, false>(p);
+}
+
+template <int G, int DT, int XV, int ROUTE, bool TRUNC>
+__global__ void __maxnreg__(RCT_CAPPED_MAXREG) bp_kernel_r16(const __grid_constant__ BpParams p) {
+    bp_body<G, DT, XV, 16, ROUTE, false, TRUNC>(p);
 }
 
 template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = false>
@@ -500,6 +506,8 @@ cudaError_t launch_one(const LaunchConfig &c, const BpParams &p, cudaStream_t s)
     const dim3 grid(gx, (p.L + c.by - 1) / c.by, (zc + R - 1) / R);
     if constexpr (FRAME) {
         bp_kernel_frame<DT, XV, R, ROUTE><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
+    } else if constexpr (R == 16) {
+        bp_kernel_r16<G, DT, XV, ROUTE, TRUNC><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
     } else {
         bp_kernel<G, DT, XV, R, ROUTE, FRAME, TRUNC><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
     }

@@ -65,7 +65,10 @@ def _gups(L: int, mode: str) -> float:
     known = {}
     for gpu, entries in cache.items():
         for key, rec in entries.items():
-            l, m, i = key.split("/")
+            parts = key.split("/")
+            if len(parts) != 3:               # frame-specific entries are not serving modes
+                continue
+            l, m, i = parts
             if m == mode and i == "soft":
                 known[int(l[1:])] = float(rec["gups"])
     if known:
