@@ -78,7 +78,6 @@ __device__ __forceinline__ float load_px(const void *img, ptrdiff_t off) {
     }
 }
 
-// Per-view constants the inner loop needs, hoisted out of the z-run.
 // Bounds-checking build (-DRCT_CHECK_BOUNDS): every computed index of a staged image, of a plain-load
 // tap and of the volume is checked against its buffer before the access; a violation is counted on
 // the device (BpParams::viol) and the access is skipped -- never a trap.
@@ -89,6 +88,7 @@ __device__ __forceinline__ bool rct_in_bounds(bool ok, unsigned long long *viol)
 }
 #endif
 
+// Per-view constants the inner loop needs, hoisted out of the z-run.
 struct ViewConsts {
     float2 m_z;      // (m[2], m[6]): step of (u', v') per z voxel
     float w_z;       // m[10]
