@@ -30,6 +30,7 @@ sys.path.insert(0, str(ROOT))
 import numpy as np  # noqa: E402
 
 METRIC = "GUPS (voxel updates/s) at 512^3 x 496, FP32 projections"
+METRIC_BY_DTYPE = {"f32": METRIC, "f16": METRIC.replace("FP32", "FP16"), "bf16": METRIC.replace("FP32", "BF16")}
 UNIT = "GUPS"
 
 # DRAM bytes (read + write) of one accumulating backprojection pass (L = 512, 1248x960 views) from an ncu
@@ -48,6 +49,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fp32_L512")
+    ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32",
+                    help="storage type of the projections for the timed step (FP32 is the headline)")
     ap.add_argument("--no-variants", action="store_true", help="skip the precision variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -158,9 +161,9 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
 
 
-def workload_config(name: str, w) -> dict:
-    return {"workload": f"{name}: L={w.L}^3 volume, {w.n_views} views of {w.geom.det_w}x{w.geom.det_h} FP32 "
-                        f"projections, seeded ellipsoid phantom",
+def workload_config(name: str, w, dtype: str = "f32") -> dict:
+    return {"workload": f"{name}: L={w.L}^3 volume, {w.n_views} views of {w.geom.det_w}x{w.geom.det_h} "
+                        f"{dtype.upper()} projections, seeded ellipsoid phantom",
             "L": w.L, "n_views": w.n_views, "det": [w.geom.det_w, w.geom.det_h], "seed": w.seed}
 
 
@@ -281,6 +284,42 @@ def prefilter_leg(workload: str, dev, stream, peaks: dict, bp_ms: float) -> dict
     return out
 
 
+def live_warp_fraction(w, tun: dict, n_warps: int = 3000, n_views: int = 24, seed: int = 5) -> float:
+    """Fraction of (warp, view) pairs the kernel's clip test keeps, estimated on sampled warps from the
+    geometry (FP64): a warp of 32 consecutive threads covers XV x-voxels per thread, its threads'
+    (x, y) positions and a z-run of R; it fetches for a view when some voxel's floor cell has a tap on the
+    detector.  The rest of the updates issue no gather."""
+    rng = np.random.default_rng(seed)
+    L, bx, by, xv, R = w.L, tun["block_x"], tun["block_y"], tun["xvec"], tun["zrun"]
+    lane = np.arange(32)
+    views = rng.choice(w.n_views, size=min(n_views, w.n_views), replace=False)
+    live = 0
+    total = 0
+    for _ in range(n_warps):
+        # a random block, warp and z-run
+        gx, gy = rng.integers(0, -(-L // (bx * xv))), rng.integers(0, -(-L // by))
+        warp = rng.integers(0, (bx * by) // 32)
+        t = warp * 32 + lane
+        x = (gx * bx + t % bx) * xv
+        y = gy * by + t // bx
+        z0 = rng.integers(0, -(-L // R)) * R
+        X = (x[:, None] + np.arange(xv)[None, :]).reshape(-1)
+        Y = np.repeat(y, xv)
+        P = np.array([[w.origin[0] + xx * w.spacing[0], w.origin[1] + yy * w.spacing[1],
+                       w.origin[2] + zz * w.spacing[2], 1.0]
+                      for xx, yy in zip(X, Y) if xx < L and yy < L for zz in range(z0, min(z0 + R, L))])
+        if P.size == 0:
+            continue
+        for k in views:
+            uvw = P @ w.geom.matrices[k].T
+            i0 = np.floor(uvw[:, 0] / uvw[:, 2])
+            j0 = np.floor(uvw[:, 1] / uvw[:, 2])
+            on = (i0 >= -1) & (i0 <= w.geom.det_w - 1) & (j0 >= -1) & (j0 <= w.geom.det_h - 1)
+            live += bool(on.any())
+            total += 1
+    return live / max(total, 1)
+
+
 def k_sweep(dev, stream, peaks: dict) -> dict:
     """Views per pass K against the volume stream at L = 1024 x 496: the volume is read and written once per
     pass (8/K bytes of HBM per voxel update), so small K is HBM-bound and large K fetch-bound."""
@@ -332,14 +371,20 @@ def run_ours(args, dist: Dist) -> dict | None:
 
     w = synth.workloads.named(args.workload)
     proj = w.projections(device=dev)                    # FP32, device resident
+    codes = {"f32": rct.RCT_PROJ_F32, "f16": rct.RCT_PROJ_F16, "bf16": rct.RCT_PROJ_BF16}
+    data = proj                                         # the timed step's projections, in the storage type
+    if args.dtype != "f32":
+        data = torch.empty(proj.shape, dtype={"f16": torch.float16, "bf16": torch.bfloat16}[args.dtype], device=dev)
+        rct.rct_convert_projections(proj, data, proj.numel(), codes[args.dtype], stream)
     torch.cuda.synchronize()
-    tun = tuning.lookup(w.L, "f32", "soft")
+    tun = tuning.lookup(w.L, args.dtype, "soft")
     bp = rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views)
-    bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(**tun)
+    bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_precision(codes[args.dtype], rct.RCT_INTERP_SOFT)
+    bp.set_tuning(**tun)
 
     def step():
         bp.reset(stream)
-        bp.backproject(proj, 0, w.n_views, stream)
+        bp.backproject(data, 0, w.n_views, stream)
 
     for _ in range(args.warmup):
         step()
@@ -383,28 +428,43 @@ def run_ours(args, dist: Dist) -> dict | None:
     px_per_voxel = min(8.0, (w.geom.sdd / w.geom.sid) * float(w.spacing[0]) / w.geom.pitch)
     route = {rct.RCT_GATHER_LDG: "ldg", rct.RCT_GATHER_MIX: "mix", rct.RCT_GATHER_QUAD: "qld",
              rct.RCT_GATHER_PAIR: "pld"}.get(tun.get("gather"), "tex")
-    probe = lambda mode: round(rct.rct_probe_texture(mode, rct.RCT_PROJ_F32, px_per_voxel, px_per_voxel, 4096) / 1e9, 1)
+    probe = lambda mode, code=rct.RCT_PROJ_F32: round(
+        rct.rct_probe_texture(mode, code, px_per_voxel, px_per_voxel, 4096) / 1e9, 1)
     probes = {"tex_tld4": probe(0), "ldg4": probe(3), "quad": probe(4), "pair": probe(5)}
-    # The gather needs four FP32 texels (16 B) per update from the L1/texture path.  Its ceiling is
-    # the L1 load data path: 128 B per clock per SM x SMs x the SM clock measured during the run.
+    texel = 4 if args.dtype == "f32" else 2
+    # The gather needs four texels (16 B FP32, 8 B 16-bit) per update from the L1/texture path.  Its
+    # ceiling is the L1 load data path: 128 B per clock per SM x SMs x the SM clock measured during the run.
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     l1_peak = 128.0 * sms * sm_mhz * 1e6 / 1e9                        # GB/s
-    gather_gbs = kernel_gups * 16.0                                   # GB/s of algorithmic texel bytes
+    gather_gbs = kernel_gups * 4 * texel                              # GB/s of algorithmic texel bytes
     vol_bytes = 4 * w.L ** 3
-    img_bytes = 4 * w.geom.det_w * w.geom.det_h
+    img_bytes = texel * w.geom.det_w * w.geom.det_h
     # per step: the first pass writes only, later passes read and write; each view's image is read once
     bytes_per_step = vol_bytes * (1 + 2 * (passes_per_step - 1)) + img_bytes * w.n_views
     bytes_per_launch = bytes_per_step / passes_per_step
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved_gbs = bytes_per_launch / avg_kernel_s / 1e9
     traffic = TRAFFIC.get(json.dumps(tun, sort_keys=True)) if w.L == 512 and w.n_views == 496 else None
+    # texture route: one tld4 gather per voxel update against the gather rate the probe measures for the
+    # storage type of the step (the texture unit, not the load/store data path, fetches these cells)
+    live = live_warp_fraction(w, tun)
+    if route == "tex" and args.dtype != "f32":
+        tld4_peak = probe(0, codes[args.dtype])
+        fetches = kernel_gups * live                                  # gathers issued per second (G/s)
+        tex_view = {"achieved": round(fetches, 1), "peak": tld4_peak, "unit": "Gfetch/s",
+                    "frac": round(fetches / tld4_peak, 4),
+                    "what": "tld4 gathers issued: voxel updates of warps the clip test keeps",
+                    "peak_source": f"measured in this run: rct_probe_texture tld4 of {args.dtype.upper()} texels"}
+    else:
+        tex_view = None
     # issue view: 4 warp instructions per clock per SM against the method's ~20 issue slots per voxel update
     # (3 incremental adds, reciprocal, 2 multiplies, floor and fraction, 3 lerps, r^2, accumulate, address math)
     issue_peak_gups = 4 * 32 * sms * sm_mhz * 1e6 / 20.0 / 1e9
     roofline = {"bound": "l1tex", "achieved": round(gather_gbs, 1), "peak": round(l1_peak, 1), "unit": "GB/s",
                 "frac": round(gather_gbs / l1_peak, 4), "traffic": traffic,
-                "what": "algorithmic gather bytes (four FP32 texels per voxel update) through the L1 load data path",
+                "what": (f"algorithmic gather bytes (four {args.dtype.upper()} texels per voxel update) through the "
+                         "L1 load data path"),
                 "peak_source": (f"derived from unit counts: 128 B/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz "
                                 "(median SM clock sampled during the timed region)"),
                 "kernel": f"bp_kernel, {route} route", "kernel_gups": round(kernel_gups, 1),
@@ -414,15 +474,19 @@ def run_ours(args, dist: Dist) -> dict | None:
                           "frac": round(kernel_gups / issue_peak_gups, 4),
                           "peak_source": "derived: 4 warp-instr/clk/SM x 32 lanes x SMs x SM clock / 20 issue slots "
                                          "per voxel update"},
+                "live_warp_fraction": round(live, 4),
+                "issued_gather_gbs": round(gather_gbs * live, 1),
+                "tex": tex_view,
                 "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                         "frac": round(achieved_gbs / hbm_peak, 4), "algorithmic_bytes_per_launch": int(bytes_per_launch),
                         "peak_source": "measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "fallback"}}
 
     result = {
-        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "metric": METRIC_BY_DTYPE[args.dtype], "value": round(value, 2), "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(args.workload, w), tuning=tun, parallelism=f"replicas x{dist.world}",
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": dict(workload_config(args.workload, w, args.dtype), tuning=tun, parallelism=f"replicas x{dist.world}",
                        l2="inputs larger than L2 (2.4 GB projections, volume >= 512 MB); no flush"),
         "roofline": roofline,
         "clocks": clk,
@@ -431,8 +495,8 @@ def run_ours(args, dist: Dist) -> dict | None:
 
     # --- end to end through the public API with host buffers
     if not args.no_e2e:
-        pinned = torch.empty(proj.shape, dtype=torch.float32, pin_memory=True)
-        pinned.copy_(proj)
+        pinned = torch.empty(data.shape, dtype=data.dtype, pin_memory=True)
+        pinned.copy_(data)
         vol_host = torch.empty((w.L,) * 3, dtype=torch.float32, pin_memory=True)
         for _ in range(max(1, args.warmup // 2)):
             bp.reset(stream)
@@ -455,16 +519,17 @@ def run_ours(args, dist: Dist) -> dict | None:
         c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         vol_dev = torch.empty((w.L,) * 3, dtype=torch.float32, device=dev)
         c0.record(stream)
-        proj.copy_(pinned, non_blocking=True)
+        data.copy_(pinned, non_blocking=True)
         c1.record(stream)
         vol_host.copy_(vol_dev, non_blocking=True)
         c2.record(stream)
         torch.cuda.synchronize()
-        h2d_gbs = pinned.numel() * 4 / (c0.elapsed_time(c1) / 1e3) / 1e9
+        h2d_gbs = pinned.numel() * pinned.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9
         d2h_gbs = vol_host.numel() * 4 / (c1.elapsed_time(c2) / 1e3) / 1e9
         del vol_dev
         result["e2e"] = {"value": round(dist.sum(float(w.updates * e_steps)) / (e_ms / 1e3) / 1e9, 2), "unit": UNIT,
-                         "h2d_bytes_per_step": int(pinned.numel() * 4), "d2h_bytes_per_step": int(vol_host.numel() * 4),
+                         "h2d_bytes_per_step": int(pinned.numel() * pinned.element_size()),
+                         "d2h_bytes_per_step": int(vol_host.numel() * 4),
                          "steps": e_steps,
                          "api": "rct_backproject_host_read (pinned host buffers; the volume read-back overlaps the last pass)",
                          "ms_per_step": round(e_ms / e_steps, 3),
@@ -492,7 +557,7 @@ def run_ours(args, dist: Dist) -> dict | None:
         result["variants_note"] = ("GUPS per precision variant on the same workload; error vs the FP64 oracle on "
                                    f"FP32 projections over {check_idx.size} sampled voxels (a full z-plane + random)")
 
-    del proj
+    del proj, data
     torch.cuda.empty_cache()
     if dist.rank == 0 and not args.no_prefilter:
         result["prefilter"] = prefilter_leg(args.workload, dev, stream, peaks, result["ms_per_step"])
@@ -537,10 +602,11 @@ def run_reference(args, dist: Dist) -> dict | None:
             rates.append(gups)
     value = statistics.median(rates)
     ms_per_step = w.updates / (value * 1e9) * 1e3
-    return {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+    return {"metric": METRIC_BY_DTYPE[args.dtype], "value": round(value, 4), "unit": UNIT, "n_gpus": dist.world,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": dict(workload_config(args.workload, w), per_step_sample=sample),
+            "config": dict(workload_config(args.workload, w, args.dtype), per_step_sample=sample),
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
