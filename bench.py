@@ -34,11 +34,14 @@ METRIC_BY_DTYPE = {"f32": METRIC, "f16": METRIC.replace("FP32", "FP16"), "bf16":
 UNIT = "GUPS"
 
 # DRAM bytes (read + write) of one accumulating backprojection pass (L = 512, 1248x960 views) from an ncu
-# capture of that launch, keyed by the tuning it ran with; a changed kernel or tuning has no entry
-# (traffic reported as null).  Source: profiles/bp_kernel_pair_f32_L512_ncu_full.md.
+# capture of that launch, keyed by storage type and the tuning it ran with; a changed kernel or tuning has no
+# entry (traffic reported as null).  Sources: profiles/bp_kernel_pair_f32_L512_ncu_full.md (FP32, pair route)
+# and profiles/bp_kernel_tld4_f16_L512_ncu_full.md (FP16, tld4 route).
 TRAFFIC: dict = {
-    '{"block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0, "views_per_pass": 24, "xvec": 1, "zrun": 8}':
+    'f32 {"block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0, "views_per_pass": 24, "xvec": 1, "zrun": 8}':
         787_052_288 + 482_466_816,
+    'f16 {"block_x": 8, "block_y": 16, "gather": 2, "tex_zrun": 0, "views_per_pass": 16, "xvec": 1, "zrun": 8}':
+        576_451_072 + 482_307_840,
 }
 
 
@@ -193,6 +196,18 @@ def oracle_rate(w, host_proj, target_s: float, max_planes: int | None = None):
     sample = (f"{planes} of {L} z-planes x {w.n_views} views ({updates:.3e} updates, {dt:.1f} s, "
               f"FP64 oracle, OpenMP over planes)")
     return updates / dt / 1e9, threads, sample
+
+
+def oracle_rate_one_core(w, host_proj, planes: int = 1):
+    """The same oracle on one thread over `planes` middle z-planes x all views; returns (GUPS, sample text)."""
+    import oracle
+    z0 = w.L // 2
+    t = time.perf_counter()
+    oracle.backproject(w.L, w.geom.det_w, w.geom.det_h, w.geom.matrices, w.origin, w.spacing, host_proj,
+                       z_range=(z0, z0 + planes), n_threads=1)
+    dt = time.perf_counter() - t
+    updates = planes * w.L * w.L * w.n_views
+    return updates / dt / 1e9, f"{planes} z-plane(s) x {w.n_views} views on 1 thread ({dt:.1f} s)"
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -445,7 +460,8 @@ def run_ours(args, dist: Dist) -> dict | None:
     bytes_per_launch = bytes_per_step / passes_per_step
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved_gbs = bytes_per_launch / avg_kernel_s / 1e9
-    traffic = TRAFFIC.get(json.dumps(tun, sort_keys=True)) if w.L == 512 and w.n_views == 496 else None
+    traffic = (TRAFFIC.get(f"{args.dtype} {json.dumps(tun, sort_keys=True)}")
+               if w.L == 512 and w.n_views == 496 else None)
     # texture route: one tld4 gather per voxel update against the gather rate the probe measures for the
     # storage type of the step (the texture unit, not the load/store data path, fetches these cells)
     live = live_warp_fraction(w, tun)
@@ -480,6 +496,13 @@ def run_ours(args, dist: Dist) -> dict | None:
                 "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                         "frac": round(achieved_gbs / hbm_peak, 4), "algorithmic_bytes_per_launch": int(bytes_per_launch),
                         "peak_source": "measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "fallback"}}
+    if tex_view is not None:
+        # the texture route's gathers go through the texture pipe, not the load data path: its issued-gather
+        # rate against the measured tld4 rate is the headline figure; the byte view moves to a sub-object
+        lsu = {k: roofline.pop(k) for k in ("achieved", "peak", "unit", "frac", "what", "peak_source")}
+        roofline = dict({"bound": "l1tex", **{k: tex_view[k] for k in ("achieved", "peak", "unit", "frac", "what",
+                                                                         "peak_source")}},
+                        **{k: v for k, v in roofline.items() if k != "bound"}, lsu_bytes=lsu)
 
     result = {
         "metric": METRIC_BY_DTYPE[args.dtype], "value": round(value, 2), "unit": UNIT, "n_gpus": dist.world,
@@ -548,7 +571,7 @@ def run_ours(args, dist: Dist) -> dict | None:
         for dt, it, fr, tr in [("f32", "soft", "global", False), ("f32", "soft", "block", False),
                                ("f32", "soft", "global", True), ("f16", "soft", "global", False),
                                ("bf16", "soft", "global", False), ("f16", "tex", "global", False),
-                               ("f32", "tex", "global", False)]:
+                               ("bf16", "tex", "global", False), ("f32", "tex", "global", False)]:
             # the error is stated against the FP64 oracle on the FP32 projections (with the same index rule)
             name = f"{dt}_{it}" + ("_block_frame" if fr == "block" else "") + ("_rabbitct_trunc" if tr else "")
             variants[name] = measure_variant(w, proj, dt, it, max(2, args.steps // 2), 1, stream,
@@ -578,8 +601,10 @@ def run_ours(args, dist: Dist) -> dict | None:
 
     if dist.rank == 0 and not args.no_cpu_baseline:
         gups, cores, sample = oracle_rate(w, host, args.cpu_seconds)
+        one, one_sample = oracle_rate_one_core(w, host)
         result["cpu_baseline"] = {"value": round(gups, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-                                  "sample": sample}
+                                  "sample": sample,
+                                  "single_thread": {"value": round(one, 4), "unit": UNIT, "sample": one_sample}}
     return result
 
 
