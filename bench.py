@@ -525,30 +525,36 @@ def run_ours(args, dist: Dist) -> dict | None:
             bp.reset(stream)
             bp.backproject_host_read(pinned, vol_host, 0, w.n_views, stream)
         torch.cuda.synchronize()
-        e_steps = max(2, args.steps // 2)
+        vol_dev = torch.empty((w.L,) * 3, dtype=torch.float32, device=dev)
+
+        def plain_copy_gbs():
+            # plain copy rates on this host link, to read the end-to-end number against
+            c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            c0.record(stream)
+            data.copy_(pinned, non_blocking=True)
+            c1.record(stream)
+            vol_host.copy_(vol_dev, non_blocking=True)
+            c2.record(stream)
+            torch.cuda.synchronize()
+            return {"h2d": round(pinned.numel() * pinned.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9, 1),
+                    "d2h": round(vol_host.numel() * 4 / (c1.elapsed_time(c2) / 1e3) / 1e9, 1)}
+
+        copy_before = plain_copy_gbs()
+        e_steps = max(2, args.steps)
         dist.barrier()
         t0 = time.perf_counter()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(e_steps):
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(e_steps + 1)]
+        marks[0].record(stream)
+        for i in range(e_steps):
             bp.reset(stream)
             bp.backproject_host_read(pinned, vol_host, 0, w.n_views, stream)
-        a1.record(stream)
+            marks[i + 1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        e_ms = max(a0.elapsed_time(a1), wall * 1e3)
+        e_ms = max(marks[0].elapsed_time(marks[-1]), wall * 1e3)
         e_ms = dist.max(e_ms)
-        # plain copy rates on this host link, to read the end-to-end number against
-        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        vol_dev = torch.empty((w.L,) * 3, dtype=torch.float32, device=dev)
-        c0.record(stream)
-        data.copy_(pinned, non_blocking=True)
-        c1.record(stream)
-        vol_host.copy_(vol_dev, non_blocking=True)
-        c2.record(stream)
-        torch.cuda.synchronize()
-        h2d_gbs = pinned.numel() * pinned.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9
-        d2h_gbs = vol_host.numel() * 4 / (c1.elapsed_time(c2) / 1e3) / 1e9
+        per_step = sorted(marks[i].elapsed_time(marks[i + 1]) for i in range(e_steps))
+        copy_after = plain_copy_gbs()
         del vol_dev
         result["e2e"] = {"value": round(dist.sum(float(w.updates * e_steps)) / (e_ms / 1e3) / 1e9, 2), "unit": UNIT,
                          "h2d_bytes_per_step": int(pinned.numel() * pinned.element_size()),
@@ -556,7 +562,9 @@ def run_ours(args, dist: Dist) -> dict | None:
                          "steps": e_steps,
                          "api": "rct_backproject_host_read (pinned host buffers; the volume read-back overlaps the last pass)",
                          "ms_per_step": round(e_ms / e_steps, 3),
-                         "plain_copy_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)}}
+                         "step_ms": {"min": round(per_step[0], 3), "median": round(statistics.median(per_step), 3),
+                                     "max": round(per_step[-1], 3)},
+                         "plain_copy_gbs": {"before": copy_before, "after": copy_after}}
         del pinned, vol_host
 
     bp.close()
