@@ -310,7 +310,12 @@ RCT_API size_t rct_footprint_bytes(int L, int det_w, int det_h, int proj_dtype, 
  * first pass after a reset) are frozen into the graph; the caller keeps the
  * buffers it names alive while the graph exists.  rct_graph_launch replays
  * it on any stream; rct_graph_destroy releases it.  The default stream
- * cannot be captured (RCT_EINVAL).
+ * cannot be captured (RCT_EINVAL).  The graph also points at state the
+ * contexts own; rct_graph_launch returns RCT_ESTATE, and launches nothing,
+ * once one of them has been destroyed or has replaced that state since the
+ * capture: staging reallocated (a larger views_per_pass, another storage type
+ * or gather route), a new geometry (rct_set_geometry*) or new filter tables
+ * (rct_set_filter).  Capture again after such a change.
  */
 typedef struct rct_graph rct_graph;
 RCT_API rct_status rct_graph_begin(void *stream);

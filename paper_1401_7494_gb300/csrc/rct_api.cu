@@ -3,12 +3,17 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "../../include/rct.h"
@@ -92,6 +97,8 @@ rct_status rct::rct_internal_fail(rct_status code, const char *fmt, ...) {
 struct rct_ctx {
     int L = 0, W = 0, H = 0, n_views = 0;
     int device = 0;
+    uint64_t id = 0;                // registry key (graphs check their contexts through it)
+    uint64_t gen = 0;               // bumped whenever device state a captured graph points at is replaced
     float *vol = nullptr;
     bool vol_zero_pending = true;   // the volume is logically zero; the next pass overwrites
 
@@ -143,6 +150,32 @@ struct rct_ctx {
 };
 
 namespace {
+
+// Registry of live contexts and the state generation each one is at.  A CUDA graph freezes device
+// pointers (staging arrays and buffers, filter tables) and reads tables in place (block-frame geometry);
+// a graph remembers the (context, generation) pairs it was captured with and refuses to launch when one
+// of its contexts has since been destroyed or has replaced such state.
+std::mutex g_reg_mu;
+std::unordered_map<uint64_t, uint64_t> g_live;                 // context id -> generation
+std::atomic<uint64_t> g_next_id{1};
+thread_local int g_capturing = 0;                              // rct_graph_begin calls open on this thread
+thread_local std::vector<std::pair<uint64_t, uint64_t>> g_captured;
+
+void bump(rct_ctx *c) {
+    std::lock_guard<std::mutex> lk(g_reg_mu);
+    g_live[c->id] = ++c->gen;
+}
+
+// Called by every call that enqueues work for a context: records it when `s` is being captured.
+void note_capture(const rct_ctx *c, void *stream) {
+    if (g_capturing <= 0 || !stream) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    if (cs == cudaStreamCaptureStatusActive) g_captured.emplace_back(c->id, c->gen);
+}
 
 int kernel_kind(const rct_ctx *c) { return c->interp == RCT_INTERP_TEX ? G_TEXLIN : G_SOFT; }
 
@@ -217,7 +250,15 @@ rct_status check_ctx(const rct_ctx *c) {
     return RCT_OK;
 }
 
+// Passes already queued may still read a staging resource that is about to be replaced (a larger K, another
+// storage type): wait for them first.  Replacements happen on shape changes only, never per call.
+void quiesce(const rct_ctx *) { (void)cudaDeviceSynchronize(); }
+
 void free_slots(rct_ctx *c) {
+    if (!c->slots.empty()) {
+        quiesce(c);
+        bump(c);
+    }
     for (Slot &s : c->slots) {
         if (s.tex) cudaDestroyTextureObject(s.tex);
         if (s.arr) cudaFreeArray(s.arr);
@@ -290,7 +331,11 @@ rct_status ensure_quads(rct_ctx *c, int n_slots) {
     if (!uses_quad(c)) return RCT_OK;
     const size_t need = (size_t)n_slots * layout_bytes(c);
     if (c->quad_alloc >= need) return RCT_OK;
-    if (c->quad_buf) cudaFree(c->quad_buf);
+    if (c->quad_buf) {
+        quiesce(c);
+        bump(c);
+        cudaFree(c->quad_buf);
+    }
     c->quad_buf = nullptr;
     c->quad_alloc = 0;
     cudaError_t e = cudaMalloc(&c->quad_buf, need);
@@ -305,7 +350,11 @@ void *quad_slot(const rct_ctx *c, int slot) {
 
 rct_status ensure_widen(rct_ctx *c, size_t elems) {
     if (c->widen_elems >= elems) return RCT_OK;
-    if (c->widen_buf) cudaFree(c->widen_buf);
+    if (c->widen_buf) {
+        quiesce(c);
+        bump(c);
+        cudaFree(c->widen_buf);
+    }
     c->widen_buf = nullptr;
     c->widen_elems = 0;
     cudaError_t e = cudaMalloc(&c->widen_buf, elems * sizeof(float));
@@ -425,7 +474,11 @@ rct_status ensure_host_staging(rct_ctx *c) {
     if ((st = ensure_quads(c, 2 * K))) return st;
     const bool linear = host_needs_linear(c);
     if (linear && c->lin_stage_bytes < 2 * K * view_bytes) {
-        if (c->lin_stage) cudaFree(c->lin_stage);
+        if (c->lin_stage) {
+            quiesce(c);
+            bump(c);
+            cudaFree(c->lin_stage);
+        }
         c->lin_stage = nullptr;
         c->lin_stage_bytes = 0;
         cudaError_t e = cudaMalloc(&c->lin_stage, 2 * K * view_bytes);
@@ -566,11 +619,20 @@ rct_ctx *rct_create(int L, int det_w, int det_h, int n_views) {
         return nullptr;
     }
 #endif
+    c->id = g_next_id.fetch_add(1);
+    {
+        std::lock_guard<std::mutex> lk(g_reg_mu);
+        g_live[c->id] = c->gen;
+    }
     return c;
 }
 
 void rct_destroy(rct_ctx *c) {
     if (!c) return;
+    {
+        std::lock_guard<std::mutex> lk(g_reg_mu);
+        g_live.erase(c->id);
+    }
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
@@ -617,6 +679,7 @@ rct_status rct_set_geometry(rct_ctx *c, const double *matrices, const double ori
     // Passes already queued with a previous geometry read the block-frame table when they run:
     // let them finish before it is overwritten (a fresh context has none).
     if (c->launches > 0) RCT_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    if (c->geometry_set) bump(c);   // graphs captured before read the table in place
     if ((st = ensure_copy_machinery(c))) return st;
     RCT_CUDA(cudaMemcpyAsync(c->geo_dev, geo.data(), sizeof(ViewGeo) * c->n_views, cudaMemcpyHostToDevice,
                              c->copy_stream), "cudaMemcpyAsync(geometry)");
@@ -685,6 +748,7 @@ rct_status rct_set_filter(rct_ctx *c, double sdd, double pitch, const double *pr
         pp[v] = make_float2(static_cast<float>(principal[2 * v]), static_cast<float>(principal[2 * v + 1]));
     // Filter launches already queued read the old tables: let them finish before they are replaced.
     RCT_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    if (c->filter_set) bump(c);     // graphs captured before point at the old tables
     if (c->filt_twiddle) cudaFree(c->filt_twiddle);
     if (c->filt_spectrum) cudaFree(c->filt_spectrum);
     if (c->filt_principal) cudaFree(c->filt_principal);
@@ -725,6 +789,7 @@ rct_status rct_filter_projections(rct_ctx *c, const float *d_raw, void *d_out, i
         return fail(RCT_EINVAL, "views [%d, %lld) outside [0, %d)", first_view, (long long)first_view + n, c->n_views);
     if (n == 0) return RCT_OK;
     if (!d_raw || !d_out) return fail(RCT_EINVAL, "null projection pointer");
+    note_capture(c, stream);
     const size_t px = (size_t)c->W * c->H * n;
     if (out_dtype != RCT_PROJ_F32) {     // a narrower output written in place would overwrite unread input
         const char *r0 = reinterpret_cast<const char *>(d_raw), *r1 = r0 + px * sizeof(float);
@@ -839,9 +904,9 @@ rct_status rct_get_tuning(const rct_ctx *c, rct_tuning *out) {
 }
 
 rct_status rct_reset_volume(rct_ctx *c, void *stream) {
-    (void)stream;
     rct_status st = check_ctx(c);
     if (st) return st;
+    note_capture(c, stream);
     c->vol_zero_pending = true;
     return RCT_OK;
 }
@@ -856,6 +921,7 @@ static rct_status materialise_zero(rct_ctx *c, cudaStream_t s) {
 rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n, void *stream) {
     rct_status st = check_ctx(c);
     if (st) return st;
+    note_capture(c, stream);
     if ((st = validate_range(c, d_proj, first_view, n))) return st;
     if (n == 0) return RCT_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1009,6 +1075,7 @@ rct_status backproject_host_impl(rct_ctx *c, const void *h_proj, int first_view,
 rct_status rct_backproject_host(rct_ctx *c, const void *h_proj, int first_view, int n, void *stream) {
     rct_status st = check_ctx(c);
     if (st) return st;
+    note_capture(c, stream);
     if ((st = validate_range(c, h_proj, first_view, n))) return st;
     if (n == 0) return RCT_OK;
     return backproject_host_impl(c, h_proj, first_view, n, stream, nullptr);
@@ -1018,6 +1085,7 @@ rct_status rct_backproject_host_read(rct_ctx *c, const void *h_proj, int first_v
                                      void *stream) {
     rct_status st = check_ctx(c);
     if (st) return st;
+    note_capture(c, stream);
     if ((st = validate_range(c, h_proj, first_view, n))) return st;
     if (!dst) return fail(RCT_EINVAL, "null destination");
     if (n == 0) return rct_read_volume(c, dst, stream);
@@ -1033,6 +1101,7 @@ rct_status rct_backproject_host_read(rct_ctx *c, const void *h_proj, int first_v
 rct_status rct_read_volume(rct_ctx *c, float *dst, void *stream) {
     rct_status st = check_ctx(c);
     if (st) return st;
+    note_capture(c, stream);
     if (!dst) return fail(RCT_EINVAL, "null destination");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((st = materialise_zero(c, s))) return st;
@@ -1044,6 +1113,7 @@ rct_status rct_read_volume(rct_ctx *c, float *dst, void *stream) {
 rct_status rct_write_volume(rct_ctx *c, const float *src, void *stream) {
     rct_status st = check_ctx(c);
     if (st) return st;
+    note_capture(c, stream);
     if (!src) return fail(RCT_EINVAL, "null source");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     RCT_CUDA(cudaMemcpyAsync(c->vol, src, (size_t)c->L * c->L * c->L * sizeof(float), cudaMemcpyDefault, s),
@@ -1101,18 +1171,22 @@ size_t rct_footprint_bytes(int L, int det_w, int det_h, int proj_dtype, int view
 struct rct_graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<std::pair<uint64_t, uint64_t>> uses;   // (context id, generation) at capture
 };
 
 rct_status rct_graph_begin(void *stream) {
     if (!stream) return fail(RCT_EINVAL, "graph capture needs a non-default stream");
     RCT_CUDA(cudaStreamBeginCapture(static_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal),
              "cudaStreamBeginCapture");
+    if (g_capturing++ == 0) g_captured.clear();
     return RCT_OK;
 }
 
 rct_status rct_graph_end(void *stream, rct_graph **out) {
     if (!stream || !out) return fail(RCT_EINVAL, "null argument");
     *out = nullptr;
+    std::vector<std::pair<uint64_t, uint64_t>> uses = g_captured;
+    if (g_capturing > 0 && --g_capturing == 0) g_captured.clear();
     cudaGraph_t g = nullptr;
     RCT_CUDA(cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &g), "cudaStreamEndCapture");
     cudaGraphExec_t exec = nullptr;
@@ -1124,12 +1198,26 @@ rct_status rct_graph_end(void *stream, rct_graph **out) {
     rct_graph *r = new rct_graph();
     r->graph = g;
     r->exec = exec;
+    std::sort(uses.begin(), uses.end());
+    uses.erase(std::unique(uses.begin(), uses.end()), uses.end());
+    r->uses = std::move(uses);
     *out = r;
     return RCT_OK;
 }
 
 rct_status rct_graph_launch(rct_graph *g, void *stream) {
     if (!g) return fail(RCT_EINVAL, "null graph");
+    {
+        std::lock_guard<std::mutex> lk(g_reg_mu);
+        for (const auto &u : g->uses) {
+            const auto it = g_live.find(u.first);
+            if (it == g_live.end())
+                return fail(RCT_ESTATE, "a context this graph was captured with has been destroyed");
+            if (it->second != u.second)
+                return fail(RCT_ESTATE, "a context this graph was captured with has replaced its staging, "
+                                        "geometry table or filter tables since: capture the graph again");
+        }
+    }
     RCT_CUDA(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), "cudaGraphLaunch");
     return RCT_OK;
 }

@@ -412,3 +412,61 @@ def test_overlapped_read_back_edge_cases(small_cases, cuda_device):
         with pytest.raises(rct.RctError) as e:
             rct.rct_backproject_host_read(bp.ctx, pinned, 0, 1, 0, None)
         assert e.value.status == rct.RCT_EINVAL
+
+
+def test_graph_refuses_to_launch_after_its_state_is_replaced(small_cases, cuda_device):
+    """A captured pass replays the direct call bit for bit; once its context reallocates the staging the
+    graph points at (a larger K), takes a new geometry, or is destroyed, launching it is RCT_ESTATE and
+    runs nothing."""
+    w, proj, _ = small_cases["L37"]
+    tun = dict(views_per_pass=4, zrun=4, gather=rct.RCT_GATHER_PAIR)
+    direct = gpu_backproject(w, proj, tuning=tun)
+    stream = torch.cuda.Stream(device=cuda_device)
+    out = torch.empty((w.L,) * 3, device=cuda_device)
+
+    def capture(bp):
+        rct.rct_prepare(bp.ctx, False)
+        bp.reset(stream)
+        rct.rct_graph_begin(stream)
+        try:
+            bp.backproject(proj, 0, w.n_views, stream)
+        finally:
+            g = rct.rct_graph_end(stream)
+        return g
+
+    for change in ("larger_k", "geometry", "destroyed"):
+        bp = rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views)
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(**tun)
+        g = capture(bp)
+        try:
+            rct.rct_graph_launch(g, stream)
+            bp.read_volume(out, stream)
+            stream.synchronize()
+            assert np.array_equal(out.cpu().numpy(), direct)
+            if change == "larger_k":
+                bp.set_tuning(**dict(tun, views_per_pass=8))
+                bp.backproject(proj, 0, w.n_views, stream)      # reallocates the pair staging
+            elif change == "geometry":
+                bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
+            else:
+                bp.close()
+            with pytest.raises(rct.RctError) as e:
+                rct.rct_graph_launch(g, stream)
+            assert e.value.status == rct.RCT_ESTATE
+            stream.synchronize()
+        finally:
+            rct.rct_graph_destroy(g)
+            bp.close()
+    # a smaller K reuses the staging: the graph stays valid
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(**tun)
+        g = capture(bp)
+        try:
+            bp.set_tuning(**dict(tun, views_per_pass=2))
+            bp.backproject(proj, 0, w.n_views, stream)
+            rct.rct_graph_launch(g, stream)
+            bp.read_volume(out, stream)
+            stream.synchronize()
+            assert np.array_equal(out.cpu().numpy(), direct)
+        finally:
+            rct.rct_graph_destroy(g)
