@@ -299,6 +299,34 @@ def prefilter_leg(workload: str, dev, stream, peaks: dict, bp_ms: float) -> dict
     return out
 
 
+def convert_leg(proj, stream, peaks: dict) -> dict:
+    """Narrowing of the whole projection stack to FP16 / BF16 (rct_convert_projections, one launch), timed
+    with CUDA events: 4 B read + 2 B written per pixel against the measured HBM copy rate."""
+    import torch
+    from paper_1401_7494_gb300 import rct
+    out = {}
+    n = proj.numel()
+    for name, tdt, code in [("f16", torch.float16, rct.RCT_PROJ_F16), ("bf16", torch.bfloat16, rct.RCT_PROJ_BF16)]:
+        dst = torch.empty(proj.shape, dtype=tdt, device=proj.device)
+        rct.rct_convert_projections(proj, dst, n, code, stream)
+        torch.cuda.synchronize()
+        reps, ms = 5, 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rct.rct_convert_projections(proj, dst, n, code, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1) / reps
+        gbs = n * 6 / (ms / 1e3) / 1e9
+        out[name] = {"ms": round(ms, 3), "hbm_gbs": round(gbs, 1),
+                     "hbm_frac": round(gbs / peaks.get("hbm_gbs", 6800.0), 3)}
+        del dst
+    out["note"] = (f"{n} pixels per launch (the whole stack), 6 B of HBM traffic per pixel; peak "
+                   + ("measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "fallback"))
+    return out
+
+
 def live_warp_fraction(w, tun: dict, n_warps: int = 3000, n_views: int = 24, seed: int = 5) -> float:
     """Fraction of (warp, view) pairs the kernel's clip test keeps, estimated on sampled warps from the
     geometry (FP64): a warp of 32 consecutive threads covers XV x-voxels per thread, its threads'
@@ -521,7 +549,7 @@ def run_ours(args, dist: Dist) -> dict | None:
         pinned = torch.empty(data.shape, dtype=data.dtype, pin_memory=True)
         pinned.copy_(data)
         vol_host = torch.empty((w.L,) * 3, dtype=torch.float32, pin_memory=True)
-        for _ in range(max(1, args.warmup // 2)):
+        for _ in range(max(1, args.warmup)):
             bp.reset(stream)
             bp.backproject_host_read(pinned, vol_host, 0, w.n_views, stream)
         torch.cuda.synchronize()
@@ -553,7 +581,8 @@ def run_ours(args, dist: Dist) -> dict | None:
         wall = time.perf_counter() - t0
         e_ms = max(marks[0].elapsed_time(marks[-1]), wall * 1e3)
         e_ms = dist.max(e_ms)
-        per_step = sorted(marks[i].elapsed_time(marks[i + 1]) for i in range(e_steps))
+        in_order = [marks[i].elapsed_time(marks[i + 1]) for i in range(e_steps)]
+        per_step = sorted(in_order)
         copy_after = plain_copy_gbs()
         del vol_dev
         result["e2e"] = {"value": round(dist.sum(float(w.updates * e_steps)) / (e_ms / 1e3) / 1e9, 2), "unit": UNIT,
@@ -563,11 +592,13 @@ def run_ours(args, dist: Dist) -> dict | None:
                          "api": "rct_backproject_host_read (pinned host buffers; the volume read-back overlaps the last pass)",
                          "ms_per_step": round(e_ms / e_steps, 3),
                          "step_ms": {"min": round(per_step[0], 3), "median": round(statistics.median(per_step), 3),
-                                     "max": round(per_step[-1], 3)},
+                                     "max": round(per_step[-1], 3), "in_order": [round(t, 2) for t in in_order]},
                          "plain_copy_gbs": {"before": copy_before, "after": copy_after}}
         del pinned, vol_host
 
     bp.close()
+    if dist.rank == 0:
+        result["staging"] = {"convert": convert_leg(proj, stream, peaks)}
     host = proj.cpu().numpy() if dist.rank == 0 and not (args.no_variants and args.no_cpu_baseline) else None
     if dist.rank == 0 and not args.no_variants:
         L = w.L
