@@ -108,3 +108,43 @@ def test_large_detector(cuda_device):
         # as long as the global ones and the frame brings nothing; the same scaled bar.
         got = gpu_backproject(w, proj, tuning=dict(gather=g, views_per_pass=4), frame=rct.RCT_FRAME_BLOCK)
         assert_parity(got, ref, f"4096x3072 detector, gather {g}, block frame", rms_tol=tol)
+
+
+def test_sampled_truncating_rule_L512(cuda_device):
+    """The RabbitCT cell rule at the benchmark's size and tuning, against the oracle run with the same
+    rule on sampled voxels.  Truncation jumps where a detector coordinate crosses -1 or -2; a voxel
+    within rounding of those points in some view has two valid results and is left out (FP64 test)."""
+    w = synth.workloads.named("fp32_L512")
+    proj = w.projections(device=cuda_device)
+    host = proj.cpu().numpy()
+    tun = tuning_mod.lookup(w.L, "f32", "soft")
+    stream = torch.cuda.current_stream()
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(**tun)
+        bp.set_index_rule(rct.RCT_INDEX_TRUNC)
+        bp.backproject(proj, 0, w.n_views, stream)
+        vol = torch.empty((w.L,) * 3, dtype=torch.float32, device=cuda_device)
+        bp.read_volume(vol, stream)
+        torch.cuda.synchronize()
+    del proj
+    # sampled voxels: random ones, a plane at the volume's edge in z (projects above / below the detector
+    # in part of the views) and the middle plane
+    idx = _sample_indices(w.L, seed=w.seed + 1, planes=(0, w.L // 2))
+    got = vol.view(-1)[torch.from_numpy(idx).to(cuda_device)].cpu().numpy()
+    del vol
+    L = w.L
+    z, rem = np.divmod(idx, L * L)
+    y, x = np.divmod(rem, L)
+    P = np.stack([w.origin[0] + x * w.spacing[0], w.origin[1] + y * w.spacing[1], w.origin[2] + z * w.spacing[2],
+                  np.ones(idx.size)])
+    near = np.zeros(idx.size, dtype=bool)
+    for A in np.asarray(w.geom.matrices, dtype=np.float64).reshape(-1, 3, 4):
+        u, v, ww = A @ P
+        for edge in (-1.0, -2.0):
+            near |= (np.abs(u / ww - edge) < 2e-3) | (np.abs(v / ww - edge) < 2e-3)
+    assert near.mean() < 0.01, near.mean()
+    ref = oracle.backproject_voxels(w.L, w.geom.det_w, w.geom.det_h, w.geom.matrices, w.origin, w.spacing,
+                                    host, idx, n_threads=oracle.max_threads(), index_rule=oracle.INDEX_TRUNC)
+    assert_parity(got[~near], ref[~near], f"fp32_L512 truncating rule sampled ({int((~near).sum())} voxels)")
+    floor_ref = _sampled_reference(w, host, idx)
+    assert np.linalg.norm(floor_ref - ref) / np.linalg.norm(ref) > 1e-6      # the rule changes these sums
