@@ -573,9 +573,12 @@ def run_ours(args, dist: Dist) -> dict | None:
         t0 = time.perf_counter()
         marks = [torch.cuda.Event(enable_timing=True) for _ in range(e_steps + 1)]
         marks[0].record(stream)
+        enqueue = []
         for i in range(e_steps):
+            t_call = time.perf_counter()
             bp.reset(stream)
             bp.backproject_host_read(pinned, vol_host, 0, w.n_views, stream)
+            enqueue.append((time.perf_counter() - t_call) * 1e3)
             marks[i + 1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -584,6 +587,31 @@ def run_ours(args, dist: Dist) -> dict | None:
         in_order = [marks[i].elapsed_time(marks[i + 1]) for i in range(e_steps)]
         per_step = sorted(in_order)
         copy_after = plain_copy_gbs()
+        # The same step captured once into a CUDA graph (rct_graph_*) and replayed: every replay still
+        # copies the step's projections in and the volume out, but the host enqueues one launch per step.
+        gs = torch.cuda.Stream(device=dev)
+        bp.reset(gs)
+        rct.rct_graph_begin(gs)
+        try:
+            bp.backproject_host_read(pinned, vol_host, 0, w.n_views, gs)
+        finally:
+            graph = rct.rct_graph_end(gs)
+        try:
+            for _ in range(max(1, args.warmup)):
+                rct.rct_graph_launch(graph, gs)
+            gs.synchronize()
+            gmarks = [torch.cuda.Event(enable_timing=True) for _ in range(e_steps + 1)]
+            t0 = time.perf_counter()
+            gmarks[0].record(gs)
+            for i in range(e_steps):
+                rct.rct_graph_launch(graph, gs)
+                gmarks[i + 1].record(gs)
+            gs.synchronize()
+            g_wall = time.perf_counter() - t0
+        finally:
+            rct.rct_graph_destroy(graph)
+        g_ms = dist.max(max(gmarks[0].elapsed_time(gmarks[-1]), g_wall * 1e3))
+        g_steps = [gmarks[i].elapsed_time(gmarks[i + 1]) for i in range(e_steps)]
         del vol_dev
         result["e2e"] = {"value": round(dist.sum(float(w.updates * e_steps)) / (e_ms / 1e3) / 1e9, 2), "unit": UNIT,
                          "h2d_bytes_per_step": int(pinned.numel() * pinned.element_size()),
@@ -593,7 +621,14 @@ def run_ours(args, dist: Dist) -> dict | None:
                          "ms_per_step": round(e_ms / e_steps, 3),
                          "step_ms": {"min": round(per_step[0], 3), "median": round(statistics.median(per_step), 3),
                                      "max": round(per_step[-1], 3), "in_order": [round(t, 2) for t in in_order]},
-                         "plain_copy_gbs": {"before": copy_before, "after": copy_after}}
+                         "host_enqueue_ms": [round(t, 2) for t in enqueue],
+                         "plain_copy_gbs": {"before": copy_before, "after": copy_after},
+                         "graph_replay": {
+                             "value": round(dist.sum(float(w.updates * e_steps)) / (g_ms / 1e3) / 1e9, 2),
+                             "unit": UNIT, "ms_per_step": round(g_ms / e_steps, 3),
+                             "api": "the same call captured once with rct_graph_begin/end, replayed with rct_graph_launch",
+                             "step_ms": {"min": round(min(g_steps), 3), "median": round(statistics.median(g_steps), 3),
+                                         "max": round(max(g_steps), 3), "in_order": [round(t, 2) for t in g_steps]}}}
         del pinned, vol_host
 
     bp.close()

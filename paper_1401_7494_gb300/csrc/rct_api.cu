@@ -1189,8 +1189,12 @@ rct_status rct_graph_end(void *stream, rct_graph **out) {
     if (g_capturing > 0 && --g_capturing == 0) g_captured.clear();
     cudaGraph_t g = nullptr;
     RCT_CUDA(cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &g), "cudaStreamEndCapture");
+    // Kernel nodes keep the priority of the stream they were captured on (the staging kernels run on a
+    // high-priority copy stream so that they slip in between the blocks of a running pass); a graph
+    // honours those priorities only when instantiated with this flag, else every node runs at the
+    // launch stream's priority and each staging waits for the pass ahead of it to drain.
     cudaGraphExec_t exec = nullptr;
-    cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaError_t e = cudaGraphInstantiateWithFlags(&exec, g, cudaGraphInstantiateFlagUseNodePriority);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
         return cuda_fail(e, "cudaGraphInstantiate");
