@@ -39,7 +39,7 @@ UNIT = "GUPS"
 # and profiles/bp_kernel_tld4_f16_L512_ncu_full.md (FP16, tld4 route).
 TRAFFIC: dict = {
     'f32 {"block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0, "views_per_pass": 24, "xvec": 1, "zrun": 8}':
-        787_052_288 + 482_466_816,
+        787_004_672 + 482_297_600,
     'f16 {"block_x": 8, "block_y": 16, "gather": 2, "tex_zrun": 0, "views_per_pass": 16, "xvec": 1, "zrun": 8}':
         576_451_072 + 482_307_840,
 }
