@@ -39,7 +39,7 @@ def test_full_parity_L128_496_views(cuda_device):
 
 @pytest.mark.parametrize("name,dtype,frame", [("fp32_L512", "f32", "global"), ("fp32_L512", "f32", "block"),
                                               ("fp32_L1024", "f32", "global"), ("prec_L512", "f16", "global"),
-                                              ("prec_L512", "bf16", "global")])
+                                              ("prec_L512", "bf16", "global"), ("fp32_L1024", "f16", "global")])
 def test_sampled_parity_large(cuda_device, name, dtype, frame):
     w = synth.workloads.named(name)
     proj = w.projections(device=cuda_device)
