@@ -1,0 +1,31 @@
+"""Host logic of the autotuner: the confirmation stage re-rates the fastest distinct tunings of the descent
+on a longer run and lets that run decide (no GPU: the rate function is a stand-in)."""
+from paper_1401_7494_gb300 import autotune
+
+
+def _t(k, z):
+    return {"views_per_pass": k, "zrun": z, "xvec": 1, "block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0}
+
+
+def test_confirm_best_re_rates_the_top_distinct_tunings():
+    trials = [{"tuning": _t(16, 8), "gups": 1300.0},
+              {"tuning": _t(32, 16), "gups": 1320.0},
+              {"tuning": _t(32, 16), "gups": 1320.0},          # the same tuning seen twice
+              {"tuning": _t(24, 8), "gups": 1290.0},
+              {"tuning": _t(8, 8), "gups": 1100.0}]
+    long_run = {(16, 8): 1250.0, (32, 16): 1200.0, (24, 8): 1265.0, (8, 8): 2000.0}
+    calls = []
+
+    def rate(t):
+        calls.append((t["views_per_pass"], t["zrun"]))
+        return long_run[(t["views_per_pass"], t["zrun"])]
+
+    best, gups, rows = autotune.confirm_best(trials, rate, top=3)
+    assert calls == [(32, 16), (16, 8), (24, 8)]            # fastest first, duplicates once, fourth not run
+    assert best == _t(24, 8) and gups == 1265.0              # the long run decides
+    assert [(r[1], r[2]) for r in rows] == [(1320.0, 1200.0), (1300.0, 1250.0), (1290.0, 1265.0)]
+
+
+def test_confirm_best_with_fewer_trials_than_top():
+    best, gups, rows = autotune.confirm_best([{"tuning": _t(16, 8), "gups": 5.0}], lambda t: 7.0, top=3)
+    assert best == _t(16, 8) and gups == 7.0 and len(rows) == 1
