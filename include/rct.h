@@ -63,7 +63,7 @@ typedef enum rct_status {
     RCT_ENOTSUP = 6    /* combination of options not supported */
 } rct_status;
 
-/* Element type of stored projections (spec precision variants). */
+/* Element type of stored projections (the reduced-precision storage variants). */
 typedef enum rct_proj_dtype {
     RCT_PROJ_F32 = 0,
     RCT_PROJ_F16 = 1,   /* IEEE binary16 */
