@@ -73,7 +73,7 @@ def main():
                     bp.backproject(data, 0, w.n_views, stream)
                     violations += rct.rct_debug_bound_violations(bp.ctx)
                     runs += 1
-    # Control: with the checker's staged-image limit lowered to a tenth of the image, in-bounds pair loads
+    # Control: with the bounds checks' staged-image limit lowered to a tenth of the image, in-bounds pair loads
     # past it are counted (and skipped); restored, the count stops growing.
     w = cases["L40"]
     proj = w.projections(device=dev)
