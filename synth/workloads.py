@@ -70,6 +70,8 @@ WORKLOADS = {
     "prec_L512": dict(L=512, seed=1404),
     # a short scan of the L=512 geometry for profiler captures (inputs still larger than L2)
     "profile_L512": dict(L=512, seed=1402, n_views=64),
+    # a few seconds of work anywhere: the benchmark's own plumbing under test, on the CPU
+    "tiny_L16": dict(L=16, seed=1410, n_views=8, det_w=64, det_h=48),
 }
 
 
