@@ -29,3 +29,24 @@ def test_confirm_best_re_rates_the_top_distinct_tunings():
 def test_confirm_best_with_fewer_trials_than_top():
     best, gups, rows = autotune.confirm_best([{"tuning": _t(16, 8), "gups": 5.0}], lambda t: 7.0, top=3)
     assert best == _t(16, 8) and gups == 7.0 and len(rows) == 1
+
+
+def test_tuning_cache_round_trip_and_fallbacks(tmp_path):
+    from paper_1401_7494_gb300 import tuning
+    path = tmp_path / "cache.json"
+    gpu = "Test GPU"
+    assert tuning.lookup(512, "f32", "soft", gpu=gpu, path=path) == tuning.DEFAULT        # empty cache
+    tuning.store(512, "f32", "soft", _t(24, 8), 1268.0, gpu=gpu, path=path)
+    assert tuning.lookup(512, "f32", "soft", gpu=gpu, path=path) == _t(24, 8)
+    # a block-frame key without its own entry falls back to the global-frame entry ...
+    assert tuning.lookup(512, "f32", "soft", gpu=gpu, path=path, frame="block") == _t(24, 8)
+    # ... and uses its own once stored, without touching the global one
+    tuning.store(512, "f32", "soft", _t(32, 16), 1228.0, gpu=gpu, path=path, frame="block")
+    assert tuning.lookup(512, "f32", "soft", gpu=gpu, path=path, frame="block") == _t(32, 16)
+    assert tuning.lookup(512, "f32", "soft", gpu=gpu, path=path) == _t(24, 8)
+    # other keys and other GPUs get the default
+    assert tuning.lookup(1024, "f32", "soft", gpu=gpu, path=path) == tuning.DEFAULT
+    assert tuning.lookup(512, "f16", "soft", gpu=gpu, path=path) == tuning.DEFAULT
+    assert tuning.lookup(512, "f32", "soft", gpu="Other GPU", path=path) == tuning.DEFAULT
+    # the default drops the x-vector for a volume it does not divide
+    assert tuning.lookup(37, "f32", "soft", gpu=gpu, path=path)["xvec"] == 1
