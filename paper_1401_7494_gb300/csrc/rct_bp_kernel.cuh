@@ -113,8 +113,9 @@ enum Route : int { ROUTE_TEX = 0, ROUTE_LDG = 1, ROUTE_QLD = 2, ROUTE_MIX = 3, R
 
 // Floor and fraction of q = uv * r (r = 1 / w): the packed add of 1.5 * 2^23 rounded toward -inf
 // gives t = kMagic + floor(q), whose low bits are floor(q) as an integer; f = q - floor(q), formed by one
-// FMA: exact except for q in (-0.5, 0), where the fraction needs a bit below q's last one and is rounded
-// to nearest (error <= 2^-25, in the band left of / above the detector).
+// FMA: exact except for q in (-0.5, 0) -- the half pixel before the integer shift (cu, cv) -- where the
+// fraction needs a bit below q's last one and is rounded to nearest (error <= 2^-25, below the rounding
+// that q itself carries).
 // (Folding the multiply into a directed-rounding FMA saves an instruction but measured slower:
 // the compiler's schedule of the z-run changes with it.)
 __device__ __forceinline__ void floor_frac(float2 uv, float rw, float2 &t, float2 &f) {
