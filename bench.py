@@ -494,12 +494,14 @@ def run_ours(args, dist: Dist) -> dict | None:
     # storage type of the step (the texture unit, not the load/store data path, fetches these cells)
     live = live_warp_fraction(w, tun)
     if route == "tex" and args.dtype != "f32":
-        tld4_peak = probe(0, codes[args.dtype])
+        # BF16 is staged as 16-bit unsigned texels (there is no BF16 texture format); the probe's FP16
+        # texels have the same size, which is what sets the gather rate
+        tld4_peak = probe(0, codes["f16"])
         fetches = kernel_gups * live                                  # gathers issued per second (G/s)
         tex_view = {"achieved": round(fetches, 1), "peak": tld4_peak, "unit": "Gfetch/s",
                     "frac": round(fetches / tld4_peak, 4),
                     "what": "tld4 gathers issued: voxel updates of warps the clip test keeps",
-                    "peak_source": f"measured in this run: rct_probe_texture tld4 of {args.dtype.upper()} texels"}
+                    "peak_source": "measured in this run: rct_probe_texture tld4 of 16-bit (FP16) texels"}
     else:
         tex_view = None
     # issue view: 4 warp instructions per clock per SM against the method's ~20 issue slots per voxel update
