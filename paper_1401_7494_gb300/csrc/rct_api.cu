@@ -163,7 +163,9 @@ thread_local std::vector<std::pair<uint64_t, uint64_t>> g_captured;
 
 void bump(rct_ctx *c) {
     std::lock_guard<std::mutex> lk(g_reg_mu);
-    g_live[c->id] = ++c->gen;
+    ++c->gen;
+    const auto it = g_live.find(c->id);      // absent once rct_destroy has begun: stays absent
+    if (it != g_live.end()) it->second = c->gen;
 }
 
 // Called by every call that enqueues work for a context: records it when `s` is being captured.
