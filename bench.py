@@ -407,6 +407,10 @@ def run_ours(args, dist: Dist) -> dict | None:
     import synth
     from paper_1401_7494_gb300 import rct, tuning
 
+    if dist.world > 1:
+        # the per-GPU characterisation legs (variants, pre-filter, K sweep, serving, CPU baseline) describe one
+        # GPU and would hold every replica's GPU while rank 0 runs them: at N > 1 only the step and e2e run
+        args.no_variants = args.no_prefilter = args.no_k_sweep = args.no_serve = args.no_cpu_baseline = True
     torch.cuda.set_device(dist.local)
     dev = torch.device("cuda", dist.local)
     stream = torch.cuda.current_stream()
@@ -545,6 +549,8 @@ def run_ours(args, dist: Dist) -> dict | None:
         "clocks": clk,
         "gpu_launches": int(launches),
     }
+    if dist.world > 1:
+        result["note"] = "N > 1: replicas of the timed step and e2e only; the single-GPU legs run at N = 1"
 
     # --- end to end through the public API with host buffers
     if not args.no_e2e:
