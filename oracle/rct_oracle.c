@@ -1,50 +1,62 @@
 /*
- * rct_oracle.c -- plain, slow, FP64 reference backprojector.
+ * rct_oracle.c -- plain, slow, FP64 definition of the voxel-driven
+ * backprojection.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
  * baseline leg of the benchmark may load this library.  It shares no code,
  * header, table or helper with the CUDA path, and the CUDA path never calls it.
  *
- * What it computes (the paper, Section "Algorithm", Listing 1 -- the
- * unoptimised RabbitCT reference backprojection, with its three parts):
+ * The quantity (the paper, Section "Algorithm": the RabbitCT backprojection of
+ * pre-filtered projections).  View i has a 3x4 projection matrix A_i and an
+ * image I_i of W columns by H rows.  A voxel with indices (x, y, z) has the
+ * world position (the centre of the voxel)
  *
- *   for every view i and every voxel (x, y, z) of the L^3 volume:
- *     Part 1  world position  p = (O_x + x*MM_x, O_y + y*MM_y, O_z + z*MM_z)
- *             homogeneous detector position (u, v, w) = A_i * (p, 1)
- *             de-homogenise   ix = u / w,  iy = v / w
- *             integer cell    i0 = floor(ix), j0 = floor(iy)
- *             weights         fx = ix - i0,   fy = iy - j0
- *     Part 2  four taps g(i, j) = I_i[j * W + i] when 0 <= i < W and 0 <= j < H,
- *             otherwise 0 (the ray misses the detector)
- *     Part 3  bilinear  val = (1-fy)*((1-fx) g(i0,j0)   + fx g(i0+1,j0))
- *                           +    fy *((1-fx) g(i0,j0+1) + fx g(i0+1,j0+1))
- *             inverse-square weight and update  f[z][y][x] += val / (w*w)
+ *     p = (o_x + x d_x, o_y + y d_y, o_z + z d_z)          origin o, spacing d
+ *
+ * and view i maps it projectively onto the detector:
+ *
+ *     (u, v, w) = A_i (p, 1),      detector point (s, t) = (u / w, v / w),
+ *
+ * where w (> 0 in front of the source) approximates the distance from the
+ * source and supplies the distance weight 1 / w^2.  The backprojected value
+ * of the voxel is
+ *
+ *     f(x, y, z) = sum_i  J_i(s_i, t_i) / w_i^2
+ *
+ * with J_i the bilinear interpolant of image i on its pixel grid, extended by
+ * zero beyond the detector.  On the unit grid the interpolant is the
+ * tensor-product hat sum
+ *
+ *     J(s, t) = sum_{a, b} E(a, b) h(s - a) h(t - b),    h(e) = max(0, 1 - |e|),
+ *     E(a, b) = I[b][a] for 0 <= a < W and 0 <= b < H, else 0,
+ *
+ * which only the four grid points around (s, t) reach: with a0 = floor(s),
+ * b0 = floor(t), alpha = s - a0, beta = t - b0, the weights are
+ * (1 - alpha, alpha) along s and (1 - beta, beta) along t.
  *
  * The volume is stored z-major with x fastest (index z*L*L + y*L + x), the
  * projections as n_views images of H rows by W columns, row-major.
  *
- * Readings where the listing is ambiguous (each one is also listed in the
- * design notes):
- *   - The listing truncates with an (int) cast.  That equals floor only for
- *     non-negative coordinates; for ix in (-1, 0) truncation would give
- *     i0 = 0 and a negative weight.  The oracle uses floor by default: the
- *     image is then the zero-extended grid, and the interpolant is continuous
- *     everywhere (this is also what the paper's zero-padded projection buffer,
- *     Section "SIMD Vectorization", computes).  index_rule = 1 takes the
- *     listing's truncation instead (RabbitCT compatibility): the cell is
- *     trunc(ix), and fx = ix - trunc(ix) is negative for negative ix, so the
- *     lerp extrapolates from the two taps at the image edge.
- *   - The listing's bound tests compare the row index with `width` and the
- *     column index with `height`, while it addresses rows with stride
- *     `width`.  The oracle tests the column index against W and the row
- *     index against H ("inside the projection image").
- *   - The listing reads the 3x4 matrix column-major (A[0], A[3], A[6], A[9]
- *     form u).  This oracle takes row-major matrices: A[r*4 + c].
- *   - Pixel (i, j) is the sample at detector coordinate (i, j) exactly, as
- *     the listing indexes the image with the integer cell directly.
+ * Readings where the paper's printed kernel is ambiguous (each one is also
+ * listed in the design notes):
+ *   - The printed kernel selects the cell with an (int) cast, which truncates
+ *     toward zero; that equals floor only for non-negative coordinates.  The
+ *     default here is the zero-extended interpolant above (floor), the reading
+ *     that the paper's zero-padded projection buffer (Section "SIMD
+ *     Vectorization") computes, and the one under which J is continuous.
+ *     index_rule = 1 selects the truncating cell instead (RabbitCT
+ *     compatibility): a0 = trunc(s) and alpha = s - a0, negative for negative
+ *     s, so the weights (1 - alpha, alpha) extrapolate from the two taps at the
+ *     image edge.
+ *   - The printed bounds test compares the row index with the width and the
+ *     column index with the height while rows are addressed with stride W;
+ *     here the column index is tested against W and the row index against H.
+ *   - The printed kernel reads its matrix column-major; this oracle takes
+ *     row-major matrices, A[r*4 + c].
+ *   - Pixel (a, b) is the sample at detector coordinate (a, b) exactly.
  *   - The paper's CPU kernels use an approximate reciprocal (Section "SIMD
- *     Vectorization"); the oracle divides exactly in FP64.
- *   - w <= 0 (voxel at or behind the source) cannot occur in the scan
+ *     Vectorization"); the oracle divides in FP64.
+ *   - w <= 0 (a voxel at or behind the source) cannot occur in the scan
  *     geometries used here; the oracle reports it as an error.
  *
  * Precision of stored projections: rct_oracle_round_f16 / _bf16 give the
@@ -64,75 +76,88 @@
 #define ORACLE_EBEHIND 2   /* larger codes win when several planes report */
 
 #define ORACLE_INDEX_FLOOR 0
-#define ORACLE_INDEX_TRUNC 1   /* the listing's (int) cast: toward zero (RabbitCT compatibility) */
+#define ORACLE_INDEX_TRUNC 1   /* the printed kernel's (int) cast: toward zero (RabbitCT compatibility) */
 
-/* One voxel, one view: returns the update val / w^2 of Listing 1 (Parts 1-3). */
-static int oracle_update(const double *A, const float *img, int W, int H,
-                         double wx, double wy, double wz, int index_rule, double *out)
+/* World position of the centre of voxel (x, y, z). */
+static void voxel_centre(const double *origin, const double *spacing, int x, int y, int z, double p[3])
 {
-    /* Part 1: projection and de-homogenisation */
-    double u = A[0] * wx + A[1] * wy + A[2] * wz + A[3];
-    double v = A[4] * wx + A[5] * wy + A[6] * wz + A[7];
-    double w = A[8] * wx + A[9] * wy + A[10] * wz + A[11];
-    if (!(w > 0.0)) return ORACLE_EBEHIND;
-    double ix = u / w;
-    double iy = v / w;
-    double fi0 = floor(ix);
-    double fj0 = floor(iy);
-    if (index_rule == ORACLE_INDEX_TRUNC) {     /* (int) ix: toward zero, so fx < 0 for negative ix */
-        fi0 = trunc(ix);
-        fj0 = trunc(iy);
-    }
-    double fx = ix - fi0;
-    double fy = iy - fj0;
+    p[0] = origin[0] + x * spacing[0];
+    p[1] = origin[1] + y * spacing[1];
+    p[2] = origin[2] + z * spacing[2];
+}
 
-    /* Part 2: four taps, zero outside the detector */
-    double bl = 0.0, br = 0.0, tl = 0.0, tr = 0.0;
-    if (fi0 >= -1.0 && fi0 < (double)W && fj0 >= -1.0 && fj0 < (double)H) {
-        long i0 = (long)fi0;
-        long j0 = (long)fj0;
-        int in_i0 = (i0 >= 0 && i0 < W);
-        int in_i1 = (i0 + 1 >= 0 && i0 + 1 < W);
-        int in_j0 = (j0 >= 0 && j0 < H);
-        int in_j1 = (j0 + 1 >= 0 && j0 + 1 < H);
-        if (in_j0 && in_i0) bl = img[j0 * (long)W + i0];
-        if (in_j0 && in_i1) br = img[j0 * (long)W + i0 + 1];
-        if (in_j1 && in_i0) tl = img[(j0 + 1) * (long)W + i0];
-        if (in_j1 && in_i1) tr = img[(j0 + 1) * (long)W + i0 + 1];
-    }
+/* Homogeneous detector coordinates q = A (p, 1) of a row-major 3x4 matrix. */
+static void project(const double *A, const double p[3], double q[3])
+{
+    for (int r = 0; r < 3; ++r)
+        q[r] = A[4 * r] * p[0] + A[4 * r + 1] * p[1] + A[4 * r + 2] * p[2] + A[4 * r + 3];
+}
 
-    /* Part 3: bilinear interpolation and inverse-square weight */
-    double valb = (1.0 - fx) * bl + fx * br;
-    double valt = (1.0 - fx) * tl + fx * tr;
-    double val = (1.0 - fy) * valb + fy * valt;
-    *out = val / (w * w);
+/* The zero-extended image E(a, b): pixel (a, b) on the detector, 0 beyond it. */
+static double extended_pixel(const float *img, int W, int H, double a, double b)
+{
+    if (!(a >= 0.0 && a < (double)W && b >= 0.0 && b < (double)H)) return 0.0;
+    return img[(long)b * W + (long)a];
+}
+
+/* Grid point below coordinate c and the weight of the point above it. */
+static double cell_of(double c, int index_rule, double *frac)
+{
+    double base = (index_rule == ORACLE_INDEX_TRUNC) ? trunc(c) : floor(c);
+    *frac = c - base;
+    return base;
+}
+
+/* The interpolant J(s, t): the hat-weighted sum over the 2 x 2 grid points around (s, t). */
+static double interpolant(const float *img, int W, int H, double s, double t, int index_rule)
+{
+    double alpha, beta;
+    double a0 = cell_of(s, index_rule, &alpha);
+    double b0 = cell_of(t, index_rule, &beta);
+    const double ws[2] = {1.0 - alpha, alpha};
+    const double wt[2] = {1.0 - beta, beta};
+    double sum = 0.0;
+    for (int db = 0; db < 2; ++db)
+        for (int da = 0; da < 2; ++da)
+            sum += ws[da] * wt[db] * extended_pixel(img, W, H, a0 + da, b0 + db);
+    return sum;
+}
+
+/* One view's term J(s, t) / w^2 for the voxel at world position p. */
+static int view_term(const double *A, const float *img, int W, int H, const double p[3], int index_rule,
+                     double *term)
+{
+    double q[3];
+    project(A, p, q);
+    if (!(q[2] > 0.0)) return ORACLE_EBEHIND;
+    *term = interpolant(img, W, H, q[0] / q[2], q[1] / q[2], index_rule) / (q[2] * q[2]);
     return ORACLE_OK;
 }
 
 static int check_args(int L, int W, int H, int n_views, const double *A, const double *origin,
-                      const double *spacing, const float *proj)
+                      const double *spacing, const float *proj, int index_rule)
 {
     if (L <= 0 || W <= 0 || H <= 0 || n_views < 0) return ORACLE_EINVAL;
     if (!A || !origin || !spacing || (!proj && n_views > 0)) return ORACLE_EINVAL;
+    if (index_rule != ORACLE_INDEX_FLOOR && index_rule != ORACLE_INDEX_TRUNC) return ORACLE_EINVAL;
     return ORACLE_OK;
 }
 
 /*
- * Backproject views [0, n_views) into z-planes [z_begin, z_end) of an L^3
+ * Add the terms of views [0, n_views) to z-planes [z_begin, z_end) of an L^3
  * volume.  `vol` holds (z_end - z_begin) planes of L*L doubles and is
- * accumulated into (the caller zeroes it for a fresh reconstruction).
- * Views are applied in order, one full pass over the planes per view, as the
- * reference module is called once per projection image.  Planes are
- * independent (Section "Implementation": one OpenMP task per voxel plane);
- * n_threads > 1 distributes them, which does not change any sum.
+ * accumulated into (the caller zeroes it for a fresh reconstruction).  The
+ * views are added in order, each one over all planes before the next, as the
+ * RabbitCT framework hands the module one projection at a time.  Planes are
+ * independent (the paper's parallelisation, Section "Implementation");
+ * n_threads > 1 spreads them over threads without changing any sum.
  */
 int rct_oracle_backproject(int L, int W, int H, int n_views, const double *A,
                            const double *origin, const double *spacing, const float *proj,
                            int z_begin, int z_end, int n_threads, int index_rule, double *vol)
 {
-    int rc = check_args(L, W, H, n_views, A, origin, spacing, proj);
+    int rc = check_args(L, W, H, n_views, A, origin, spacing, proj, index_rule);
     if (rc) return rc;
-    if (index_rule != ORACLE_INDEX_FLOOR && index_rule != ORACLE_INDEX_TRUNC) return ORACLE_EINVAL;
     if (z_begin < 0 || z_end > L || z_begin > z_end || !vol) return ORACLE_EINVAL;
     int status = ORACLE_OK;
     const long img_px = (long)W * H;
@@ -144,18 +169,16 @@ int rct_oracle_backproject(int L, int W, int H, int n_views, const double *A,
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1) reduction(max : status)
 #endif
         for (int z = z_begin; z < z_end; ++z) {
-            double wz = origin[2] + z * spacing[2];
-            double *vz = vol + (long)(z - z_begin) * plane;
+            double *fz = vol + (long)(z - z_begin) * plane;
             for (int y = 0; y < L; ++y) {
-                double wy = origin[1] + y * spacing[1];
                 for (int x = 0; x < L; ++x) {
-                    double wx = origin[0] + x * spacing[0];
-                    double upd;
-                    if (oracle_update(Ai, img, W, H, wx, wy, wz, index_rule, &upd) != ORACLE_OK) {
+                    double p[3], term;
+                    voxel_centre(origin, spacing, x, y, z, p);
+                    if (view_term(Ai, img, W, H, p, index_rule, &term) != ORACLE_OK) {
                         status = ORACLE_EBEHIND;
                         continue;
                     }
-                    vz[(long)y * L + x] += upd;
+                    fz[(long)y * L + x] += term;
                 }
             }
         }
@@ -164,18 +187,17 @@ int rct_oracle_backproject(int L, int W, int H, int n_views, const double *A,
 }
 
 /*
- * Same sums for a list of voxels given by flat index z*L*L + y*L + x.
- * out[k] (accumulated into) receives the sum over views [0, n_views) in view
- * order for voxel idx[k].  Used to check very large volumes on samples.
+ * The same sums for a list of voxels given by flat index z*L*L + y*L + x.
+ * out[k] (accumulated into) receives the sum over views [0, n_views), in view
+ * order, for voxel idx[k].  Used to check very large volumes on samples.
  */
 int rct_oracle_backproject_voxels(int L, int W, int H, int n_views, const double *A,
                                   const double *origin, const double *spacing, const float *proj,
                                   const int64_t *idx, int64_t n_idx, int n_threads, int index_rule,
                                   double *out)
 {
-    int rc = check_args(L, W, H, n_views, A, origin, spacing, proj);
+    int rc = check_args(L, W, H, n_views, A, origin, spacing, proj, index_rule);
     if (rc) return rc;
-    if (index_rule != ORACLE_INDEX_FLOOR && index_rule != ORACLE_INDEX_TRUNC) return ORACLE_EINVAL;
     if (n_idx < 0 || (n_idx > 0 && (!idx || !out))) return ORACLE_EINVAL;
     const long img_px = (long)W * H;
     const int64_t total = (int64_t)L * L * L;
@@ -186,22 +208,18 @@ int rct_oracle_backproject_voxels(int L, int W, int H, int n_views, const double
     for (int64_t k = 0; k < n_idx; ++k) {
         int64_t f = idx[k];
         if (f < 0 || f >= total) { status = ORACLE_EINVAL; continue; }
-        int x = (int)(f % L);
-        int y = (int)((f / L) % L);
-        int z = (int)(f / ((int64_t)L * L));
-        double wx = origin[0] + x * spacing[0];
-        double wy = origin[1] + y * spacing[1];
-        double wz = origin[2] + z * spacing[2];
-        double acc = out[k];
+        double p[3];
+        voxel_centre(origin, spacing, (int)(f % L), (int)((f / L) % L), (int)(f / ((int64_t)L * L)), p);
+        double sum = out[k];
         for (int i = 0; i < n_views; ++i) {
-            double upd;
-            if (oracle_update(A + 12L * i, proj + img_px * i, W, H, wx, wy, wz, index_rule, &upd) != ORACLE_OK) {
+            double term;
+            if (view_term(A + 12L * i, proj + img_px * i, W, H, p, index_rule, &term) != ORACLE_OK) {
                 status = ORACLE_EBEHIND;
                 continue;
             }
-            acc += upd;
+            sum += term;
         }
-        out[k] = acc;
+        out[k] = sum;
     }
     return status;
 }
