@@ -14,9 +14,10 @@
 // The scratch is a file-scope __device__ array of kScratchValues 16-bit
 // values (32 MiB).  Every GPU that loads the library holds it until the
 // process exits.  Host code must not use the array's name as an address (on
-// the host it is only a stand-in); its device address is looked up once per
-// device with cudaGetSymbolAddress, on the first call made while that
-// device is current.
+// the host it is only a stand-in); its device address is looked up with
+// cudaGetSymbolAddress on the first call made while that device is current,
+// and only a successful lookup is kept (a failed one is tried again by the
+// next call).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -36,17 +37,26 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned short g_f16_scratch[kScratchValues];
 
-std::once_flag g_scratch_once[kMaxDevices];
+std::mutex g_scratch_mu;
 void *g_scratch_addr[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices];
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device.  A successful lookup is kept for the
+// device; a failed one (for instance a first call made while a stream is being captured) is not, so a
+// later call looks again.
 cudaError_t scratch_address(int dev, unsigned short **out) {
-    std::call_once(g_scratch_once[dev], [dev]() {
-        g_scratch_err[dev] = cudaGetSymbolAddress(&g_scratch_addr[dev], g_f16_scratch);
-    });
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *a = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&a, g_f16_scratch);
+        if (e != cudaSuccess || !a) {
+            (void)cudaGetLastError();
+            *out = nullptr;
+            return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+        }
+        g_scratch_addr[dev] = a;
+    }
     *out = static_cast<unsigned short *>(g_scratch_addr[dev]);
-    return g_scratch_err[dev];
+    return cudaSuccess;
 }
 
 // FP32 -> FP16 (round to nearest even) into the scratch, one value per thread-iteration: the
@@ -79,6 +89,13 @@ extern "C" rct_status rct_backproject_f16_noalloc(int L, int det_w, int det_h, c
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return rct_internal_fail(RCT_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return rct_internal_fail(RCT_ENOTSUP, "device %d beyond %d", dev, kMaxDevices);
+    // the detector limits of rct_create (the texture-gather extents of the device)
+    int max_w = 0, max_h = 0;
+    cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture2DGatherWidth, dev);
+    cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxTexture2DGatherHeight, dev);
+    if ((max_w > 0 && det_w > max_w) || (max_h > 0 && det_h > max_h))
+        return rct_internal_fail(RCT_EINVAL, "rct_backproject_f16_noalloc: detector %dx%d exceeds %dx%d", det_w, det_h,
+                                 max_w, max_h);
     unsigned short *scratch = nullptr;
     e = scratch_address(dev, &scratch);
     if (e != cudaSuccess || !scratch)
@@ -102,6 +119,7 @@ extern "C" rct_status rct_backproject_f16_noalloc(int L, int det_w, int det_h, c
     lc.by = 8;
     BpParams p{};
     p.vol = d_volume;
+    p.vol_elems = static_cast<long long>(L) * L * L;
     p.L = L;
     p.W = det_w;
     p.H = det_h;
