@@ -34,6 +34,11 @@
  *     they share the context's staging buffers.  Distinct contexts may be
  *     used from distinct threads and streams concurrently.
  *   - The library never falls back to a CPU computation.
+ *
+ * Two more headers go with it: rct_debug.h (the bounds-checking build's
+ * counters, exported by the same library) and rct_bench.h (throughput
+ * probes, a separate measurement library librct_bench.so that the product
+ * does not load).
  */
 #ifndef RCT_H
 #define RCT_H
@@ -111,8 +116,13 @@ typedef enum rct_gather {
                              (below), so the texture and load/store pipes work side by side */
     RCT_GATHER_QUAD = 4,  /* one 128-bit load (64-bit for 16-bit data) of a staged, zero-padded "quad"
                              copy of the image whose every element holds a whole 2x2 cell */
-    RCT_GATHER_PAIR = 5   /* two 64-bit loads (32-bit for 16-bit data) of a staged, zero-padded copy
+    RCT_GATHER_PAIR = 5,  /* two 64-bit loads (32-bit for 16-bit data) of a staged, zero-padded copy
                              whose every element holds two vertically adjacent pixels */
+    RCT_GATHER_DQUAD = 6  /* FP32 only: one 128-bit load of a staged, zero-padded copy whose every
+                             element holds a cell's left column and its two horizontal differences,
+                             so both rows are interpolated along x by one packed FMA; bit for bit the
+                             sums of RCT_GATHER_QUAD and RCT_GATHER_PAIR.  RCT_ENOTSUP at the first
+                             backprojection call with 16-bit projections */
 } rct_gather;
 
 /* Kernel tuning.  Zero in any field means "keep the current value". */
@@ -137,7 +147,29 @@ typedef struct rct_tuning {
  */
 RCT_API rct_ctx *rct_create(int L, int det_w, int det_h, int n_views);
 
-/* Release every device resource of the context (synchronises its device). NULL is ignored. */
+/*
+ * A context that holds only the z planes [z_first, z_first + z_count) of the
+ * L^3 volume (a z-slab): the paper parallelises the backprojection over
+ * independent voxel planes (Section "Implementation"), and a slab context is
+ * that split as a unit of work for one GPU.  Every call behaves as on a
+ * whole-volume context restricted to those planes: the device volume, and the
+ * buffers rct_read_volume / rct_write_volume / rct_backproject_host_read
+ * exchange, hold z_count * L * L floats (plane z_first first, then z-major
+ * with x fastest); projections and matrices are the whole scan's.  When
+ * z_first is a multiple of the z-run (every z-run divides 16), each plane is
+ * bit for bit the same plane of a whole-volume context with the same tuning.
+ * NULL on failure: z_first < 0, z_count < 1 or z_first + z_count > L give
+ * RCT_EINVAL; the other failures are rct_create's.
+ */
+RCT_API rct_ctx *rct_create_slab(int L, int det_w, int det_h, int n_views, int z_first, int z_count);
+/* Writes the planes a context holds (0 and L for rct_create). */
+RCT_API rct_status rct_get_slab(const rct_ctx *ctx, int *z_first, int *z_count);
+
+/*
+ * Release every device resource of the context.  It first waits for the work
+ * enqueued for this context (not for other contexts' work); freeing device
+ * memory may still synchronise the device.  NULL is ignored.
+ */
 RCT_API void rct_destroy(rct_ctx *ctx);
 
 /*
@@ -147,7 +179,12 @@ RCT_API void rct_destroy(rct_ctx *ctx);
  * library folds origin and spacing into each matrix in FP64 on the host
  * (the paper's O and MM, Section "Algorithm") and keeps its own copies; the
  * caller's arrays may be freed on return.  RCT_EINVAL for null pointers,
- * non-finite values or non-positive spacing.
+ * non-finite values or non-positive spacing, and for a view in which a
+ * corner of the volume has w <= 0 (at or behind the source: Listing 1's
+ * 1/w^2 weight assumes every voxel in front of it) or projects 2^21 pixels
+ * or more from where the volume centre projects.  If work of this context
+ * is still queued, the call waits for it (the new geometry replaces a table
+ * those passes read); work of other contexts is not waited for.
  */
 RCT_API rct_status rct_set_geometry(rct_ctx *ctx, const double *matrices, const double origin[3],
                             const double spacing[3]);
@@ -156,8 +193,20 @@ RCT_API rct_status rct_set_geometry(rct_ctx *ctx, const double *matrices, const 
  * Choose the element type of the projections passed to rct_backproject and
  * the interpolation.  Accumulation and the 1/w^2 weight stay FP32.
  * Default: RCT_PROJ_F32, RCT_INTERP_SOFT.
+ * Paper: the RabbitCT projections are FP32 (Section "RabbitCT Benchmark"),
+ * and Part 2 of Listing 1 (Section "Algorithm") reads four FP32 pixels.
+ * 16-bit storage halves those gather bytes; the texture-unit bilinear
+ * option follows the paper's account of why GPUs are fast at this kernel
+ * (Section "Comparison to GPU Implementations").  Neither is in the
+ * paper's own kernels: they are reduced-precision variants whose error
+ * against the FP64 definition is stated, not assumed.
+ * Errors: RCT_EINVAL for an unknown dtype or interp; RCT_ENOTSUP when the
+ * context's frame or index rule needs FP32 software interpolation.
+ * Takes effect at the next call; nothing is enqueued.
  */
 RCT_API rct_status rct_set_precision(rct_ctx *ctx, int proj_dtype, int interp);
+/* The element type and interpolation set for the context (either pointer may be NULL). */
+RCT_API rct_status rct_get_precision(const rct_ctx *ctx, int *proj_dtype, int *interp);
 
 /*
  * Choose the coordinate frame (rct_frame; default RCT_FRAME_GLOBAL).  RCT_FRAME_BLOCK needs FP32
@@ -184,18 +233,6 @@ RCT_API rct_status rct_get_frame(const rct_ctx *ctx, int *frame);
  * (world position of voxel (x, y, z) = (O + x MM, O + y MM, O + z MM)).  It widens them to FP64
  * and calls rct_set_geometry, with the same errors.
  */
-/*
- * Bounds-checking build (the library compiled with -DRCT_CHECK_BOUNDS; the Python binding builds and
- * loads it when RCT_BUILD_VARIANT=check): every computed index of a staged image, of a plain-load
- * tap and of the volume is checked before the access, a violation is counted and the access
- * skipped.  rct_debug_bound_violations synchronises the device and returns the context's count;
- * RCT_ENOTSUP from the normal build.
- */
-RCT_API rct_status rct_debug_bound_violations(rct_ctx *ctx, unsigned long long *count);
-/* Checking build only: compare staged-image indices against at most staged_elems elements (0 restores
- * the real size), so that in-bounds accesses past that limit are counted and skipped -- a control
- * that the checks are live.  No access leaves its buffer.  RCT_ENOTSUP from the normal build. */
-RCT_API rct_status rct_debug_lower_bound_limit(rct_ctx *ctx, long long staged_elems);
 
 RCT_API rct_status rct_set_index_rule(rct_ctx *ctx, int rule);
 RCT_API rct_status rct_get_index_rule(const rct_ctx *ctx, int *rule);
@@ -215,7 +252,8 @@ RCT_API rct_status rct_set_geometry_rabbitct(rct_ctx *ctx, const float *matrices
  *
  * rct_set_filter stores the filter for the context: sdd and pitch (finite, > 0) and principal,
  * n_views pairs (u0, v0) in view order (copied; the caller's array may be freed on return).
- * Rows longer than 8192 pixels give RCT_ENOTSUP.  It synchronises the device (set-up call).
+ * Rows longer than 8192 pixels give RCT_ENOTSUP.  A set-up call: it waits for the work already
+ * enqueued for this context (filter launches read the tables it replaces), not for other contexts.
  *
  * rct_filter_projections filters views [first_view, first_view + n): d_raw holds n FP32 images
  * [n][H][W] on the device; d_out receives n images in out_dtype (rct_proj_dtype, rounded to
@@ -234,12 +272,25 @@ RCT_API rct_status rct_set_tuning(rct_ctx *ctx, const rct_tuning *t);
 /* Read the tuning the next launch will use (after AUTO resolution). */
 RCT_API rct_status rct_get_tuning(const rct_ctx *ctx, rct_tuning *out);
 
-/* Zero the volume.  Costs nothing on the device: the next pass overwrites instead of adding. */
+/*
+ * Zero the volume: the start of a reconstruction, before the first view is
+ * added (the RabbitCT volume starts at zero and every view's Listing 1 pass,
+ * Section "Algorithm", adds into it; layout z*L*L + y*L + x as Listing 1
+ * indexes it).  Costs nothing on the device: the next pass overwrites
+ * instead of adding (a read or write of the volume first clears it).
+ * Errors: RCT_EINVAL for a null context, RCT_ESTATE when another device is
+ * current.
+ */
 RCT_API rct_status rct_reset_volume(rct_ctx *ctx, void *stream);
 
 /*
  * Backproject views [first_view, first_view + n) into the volume, in view
- * order.  d_proj points to n device images (the first one belongs to view
+ * order: for each of those views and every voxel, Listing 1's three parts
+ * (Section "Algorithm": project with the view's matrix and de-homogenise;
+ * gather the 2x2 pixel cell, zero off the detector; interpolate bilinearly
+ * and add val / w^2 into VOL[z*L*L + y*L + x]).  Views are accumulated K
+ * at a time in registers (the tuning's views_per_pass), which changes the
+ * order of the FP32 additions but not the sum's terms.  d_proj points to n device images (the first one belongs to view
  * first_view) in the element type set by rct_set_precision.  Texture routes
  * stage each batch of K views into the context's gather arrays on an
  * internal copy stream (forked from and joined back into `stream` with
@@ -275,7 +326,13 @@ RCT_API rct_status rct_backproject_host(rct_ctx *ctx, const void *h_proj, int fi
 RCT_API rct_status rct_backproject_host_read(rct_ctx *ctx, const void *h_proj, int first_view, int n, float *dst,
                                              void *stream);
 
-/* Copy the volume (L^3 floats) to dst, host or device memory.  Enqueued on stream. */
+/*
+ * Copy the volume to dst, host or device memory: L^3 floats (z_count*L*L for a
+ * slab context, see rct_create_slab), z-major with x fastest, the index
+ * z*L*L + y*L + x of Listing 1 (Section "Algorithm").  Enqueued on stream;
+ * dst must stay valid until the stream reaches the copy (pageable host
+ * memory makes the call wait for it).  Errors: RCT_EINVAL for a null dst.
+ */
 RCT_API rct_status rct_read_volume(rct_ctx *ctx, float *dst, void *stream);
 
 /* Overwrite the volume from src (host or device, L^3 floats): restores a checkpoint. */
@@ -348,27 +405,12 @@ RCT_API rct_status rct_convert_projections(const float *d_src, void *d_dst, size
  *     u' = u - cu*w,  v' = v - cv*w,  w = w   with (u, v, w) = A (origin + (x,y,z)*spacing, 1),
  * and the integer detector shift (cu, cv): the pixel nearest to where the
  * volume centre projects (0 when that point is not in front of the source).
- * fold_out: n_views * 12 doubles; shift_out: n_views * 2 ints.
+ * fold_out: n_views * 12 doubles; shift_out: n_views * 2 ints.  RCT_EINVAL
+ * as rct_set_geometry (including the checks of the volume's corners).
  */
 RCT_API rct_status rct_fold_geometry(int L, int n_views, const double *matrices, const double origin[3],
                              const double spacing[3], double *fold_out, int *shift_out);
 
-/*
- * Throughput probes (measurement support, allocate their own small buffers).
- * rct_probe_texture: fetches per second over the whole GPU for texture fetches
- * of one kind -- mode 0 = tld4 gather, 1 = point fetch, 2 = bilinear filtered
- * fetch, 3 = four predicated global loads of the 2x2 cell (FP32 only), 4 = one
- * 16-byte quad load, 5 = two 8-byte pair loads (4 and 5: FP32 staged layouts over
- * a 1280 x 1024-element buffer that lives in L2, not L1) --
- * from a 256x256 texture (or linear image) of dtype RCT_PROJ_F32 or RCT_PROJ_F16 that
- * stays cache resident; neighbouring lanes sample stride_px apart along x and
- * each fetch advances step_px along y (stride 0..10 px, step 0..8 px, else
- * RCT_EINVAL).  rct_probe_update_stream: bytes read +
- * written per second by a float4 read-modify-write sweep over `bytes` of
- * device memory (the paper's "Node Update" benchmark, Table 1).
- */
-RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float step_px, int iters, double *rate);
-RCT_API rct_status rct_probe_update_stream(size_t bytes, double *rate);
 
 /*
  * Allocation-free backprojection (the paper has no counterpart; it exists for
@@ -382,11 +424,14 @@ RCT_API rct_status rct_probe_update_stream(size_t bytes, double *rate);
  * and backprojected with the FP16 predicated-load kernel into the caller's
  * L^3 FP32 device volume d_volume (overwritten when accumulate == 0, added to
  * otherwise).  matrices: n row-major 3x4 FP64 on the host; origin/spacing as
- * in rct_set_geometry.  Views go through the scratch in batches of up to 32;
- * one view must fit (det_w * det_h <= 16 Mi pixels), larger detectors give
- * RCT_EINVAL.  The first call on a device looks up the scratch address with
- * cudaGetSymbolAddress (make it before any stream capture); later calls only
- * enqueue work on `stream`.  All calls on a device share the one scratch:
+ * in rct_set_geometry (with its checks of the volume's corners).  Views go
+ * through the scratch in batches of up to 32; one view must fit (det_w *
+ * det_h <= 16 Mi pixels), and det_w, det_h must stay within the limits
+ * rct_create takes (the device's texture-gather extents): RCT_EINVAL
+ * otherwise.  The first call on a device looks up the scratch address with
+ * cudaGetSymbolAddress (make it before any stream capture; a lookup that
+ * fails returns RCT_ECUDA and is tried again by the next call); later calls
+ * only enqueue work on `stream`.  All calls on a device share the one scratch:
  * calls whose work may overlap on the GPU (different streams without
  * ordering) race on it and give wrong volumes; order them on one stream.
  * Nothing in the scratch has to start at zero: each batch rewrites what it

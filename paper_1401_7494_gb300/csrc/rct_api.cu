@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/rct.h"
+#include "../../include/rct_debug.h"
 #include "rct_internal.h"
 
 using namespace rct;
@@ -96,6 +97,7 @@ rct_status rct::rct_internal_fail(rct_status code, const char *fmt, ...) {
 
 struct rct_ctx {
     int L = 0, W = 0, H = 0, n_views = 0;
+    int z_first = 0, z_count = 0;   // planes of the L^3 volume this context holds (all L unless a slab)
     int device = 0;
     uint64_t id = 0;                // registry key (graphs check their contexts through it)
     uint64_t gen = 0;               // bumped whenever device state a captured graph points at is replaced
@@ -143,6 +145,12 @@ struct rct_ctx {
 
     int64_t launches = 0;
 
+    // The end of the last work enqueued for this context (recorded after every call that enqueues work
+    // outside a stream capture, and after every replay of a graph that uses the context): set-up calls
+    // that replace device state wait for it instead of for the whole device.
+    cudaEvent_t ev_done = nullptr;
+    bool done_recorded = false;
+
     // optional per-launch timing (CUDA events around every backprojection kernel)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_events;  // pairs: start, stop
@@ -156,7 +164,11 @@ namespace {
 // a graph remembers the (context, generation) pairs it was captured with and refuses to launch when one
 // of its contexts has since been destroyed or has replaced such state.
 std::mutex g_reg_mu;
-std::unordered_map<uint64_t, uint64_t> g_live;                 // context id -> generation
+struct LiveEntry {
+    uint64_t gen;
+    rct_ctx *ctx;
+};
+std::unordered_map<uint64_t, LiveEntry> g_live;                // context id -> generation, context
 std::atomic<uint64_t> g_next_id{1};
 thread_local int g_capturing = 0;                              // rct_graph_begin calls open on this thread
 thread_local std::vector<std::pair<uint64_t, uint64_t>> g_captured;
@@ -165,7 +177,7 @@ void bump(rct_ctx *c) {
     std::lock_guard<std::mutex> lk(g_reg_mu);
     ++c->gen;
     const auto it = g_live.find(c->id);      // absent once rct_destroy has begun: stays absent
-    if (it != g_live.end()) it->second = c->gen;
+    if (it != g_live.end()) it->second.gen = c->gen;
 }
 
 // Called by every call that enqueues work for a context: records it when `s` is being captured.
@@ -192,7 +204,8 @@ int tex_zrun_of(const rct_ctx *c) {
     switch (gather_of(c)) {
         case RCT_GATHER_LDG:
         case RCT_GATHER_QUAD:
-        case RCT_GATHER_PAIR: return 0;
+        case RCT_GATHER_PAIR:
+        case RCT_GATHER_DQUAD: return 0;
         case RCT_GATHER_MIX: return R <= 1 ? R : std::min(std::max(c->tune.tex_zrun, 1), R - 1);
         default: return R;
     }
@@ -201,10 +214,11 @@ int tex_zrun_of(const rct_ctx *c) {
 bool uses_tex(const rct_ctx *c) { return kernel_kind(c) == G_TEXLIN || tex_zrun_of(c) > 0; }
 
 // Staged layout the load part of the software route reads: 0 = none (texture only, or the
-// caller's linear image), 1 = quads (QUAD, MIX), 2 = vertical pairs (PAIR).
+// caller's linear image), 1 = quads (QUAD, MIX), 2 = vertical pairs (PAIR), 3 = difference quads (DQUAD).
 int load_layout(const rct_ctx *c) {
     if (kernel_kind(c) != G_SOFT || gather_of(c) == RCT_GATHER_LDG || tex_zrun_of(c) >= c->tune.zrun) return 0;
-    return gather_of(c) == RCT_GATHER_PAIR ? 2 : 1;
+    if (gather_of(c) == RCT_GATHER_PAIR) return 2;
+    return gather_of(c) == RCT_GATHER_DQUAD ? 3 : 1;
 }
 
 bool uses_quad(const rct_ctx *c) { return load_layout(c) != 0; }
@@ -214,8 +228,18 @@ size_t layout_bytes(const rct_ctx *c) {
 }
 
 cudaError_t launch_stage_layout(const rct_ctx *c, const void *src, void *dst, cudaStream_t s) {
-    return load_layout(c) == 2 ? launch_stage_pairs(src, dst, c->W, c->H, c->dtype, s)
-                               : launch_stage_quads(src, dst, c->W, c->H, c->dtype, s);
+    switch (load_layout(c)) {
+        case 2: return launch_stage_pairs(src, dst, c->W, c->H, c->dtype, s);
+        case 3: return launch_stage_dquads(static_cast<const float *>(src), dst, c->W, c->H, s);
+        default: return launch_stage_quads(src, dst, c->W, c->H, c->dtype, s);
+    }
+}
+
+// The difference-quad layout holds FP32 values only.
+rct_status check_route(const rct_ctx *c) {
+    if (gather_of(c) == RCT_GATHER_DQUAD && (c->dtype != DT_F32 || kernel_kind(c) != G_SOFT))
+        return fail(RCT_ENOTSUP, "the difference-quad gather needs FP32 projections and software interpolation");
+    return RCT_OK;
 }
 
 // The kernel reads the caller's linear image (LDG route), or BF16 must be widened before a
@@ -252,9 +276,41 @@ rct_status check_ctx(const rct_ctx *c) {
     return RCT_OK;
 }
 
+bool stream_capturing(void *stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Marks the end of the work a call just enqueued on `stream` for this context (nothing while the stream is
+// being captured: that work runs when the graph is launched, which records the mark then).
+cudaError_t mark_done(rct_ctx *c, void *stream) {
+    if (stream_capturing(stream)) return cudaSuccess;
+    if (!c->ev_done) {
+        cudaError_t e = cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaEventRecord(c->ev_done, static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) c->done_recorded = true;
+    return e;
+}
+
+// Waits until the device has finished every piece of work enqueued for this context (its passes on the
+// caller's streams and its staging on its own copy stream); other contexts' work keeps running.
+cudaError_t wait_idle(rct_ctx *c) {
+    cudaError_t e = cudaSuccess;
+    if (c->done_recorded && c->ev_done) e = cudaEventSynchronize(c->ev_done);
+    if (e == cudaSuccess && c->copy_stream) e = cudaStreamSynchronize(c->copy_stream);
+    return e;
+}
+
 // Passes already queued may still read a staging resource that is about to be replaced (a larger K, another
-// storage type): wait for them first.  Replacements happen on shape changes only, never per call.
-void quiesce(const rct_ctx *) { (void)cudaDeviceSynchronize(); }
+// storage type): wait for this context's work first.  Replacements happen on shape changes only, never per
+// call.
+void quiesce(rct_ctx *c) { (void)wait_idle(c); }
 
 void free_slots(rct_ctx *c) {
     if (!c->slots.empty()) {
@@ -381,6 +437,10 @@ LaunchConfig launch_config(const rct_ctx *c, int kind) {
 void init_params(const rct_ctx *c, BpParams *p) {
     std::memset(p, 0, sizeof *p);
     p->vol = c->vol;
+    p->vol_z0 = c->z_first;
+    p->z_base = c->z_first;
+    p->z_count = c->z_count;
+    p->vol_elems = static_cast<long long>(c->z_count) * c->L * c->L;
     p->L = c->L;
     p->W = c->W;
     p->H = c->H;
@@ -566,6 +626,21 @@ rct_status rct_fold_geometry(int L, int n_views, const double *matrices, const d
             P[k] -= cu * P[8 + k];
             P[4 + k] -= cv * P[8 + k];
         }
+        // Every voxel must lie in front of the source (w > 0), and its detector coordinate relative to
+        // the shift must stay below 2^21 pixels, where the kernels' floor (an add of 1.5 * 2^23) is
+        // exact.  (u', v', w) is affine in the voxel index and the view maps the volume's box onto the
+        // convex hull of its corners' images while w > 0 on it, so the eight corners decide both.
+        for (int corner = 0; corner < 8; ++corner) {
+            const double c3[3] = {(corner & 1) ? cen : -cen, (corner & 2) ? cen : -cen, (corner & 4) ? cen : -cen};
+            double q[3];
+            for (int r = 0; r < 3; ++r) q[r] = P[4 * r] * c3[0] + P[4 * r + 1] * c3[1] + P[4 * r + 2] * c3[2] + P[4 * r + 3];
+            if (!(q[2] > 0.0))
+                return fail(RCT_EINVAL, "view %d: a corner of the volume lies at or behind the source plane (w = %g)",
+                            v, q[2]);
+            if (!(std::fabs(q[0] / q[2]) < 2097152.0 && std::fabs(q[1] / q[2]) < 2097152.0))
+                return fail(RCT_EINVAL, "view %d: a corner of the volume projects 2^21 or more pixels from the "
+                            "detector position of the volume centre", v);
+        }
         std::memcpy(fold_out + 12 * (size_t)v, P, sizeof P);
         shift_out[2 * v] = cu;
         shift_out[2 * v + 1] = cv;
@@ -574,12 +649,21 @@ rct_status rct_fold_geometry(int L, int n_views, const double *matrices, const d
 }
 
 rct_ctx *rct_create(int L, int det_w, int det_h, int n_views) {
+    return rct_create_slab(L, det_w, det_h, n_views, 0, L);
+}
+
+rct_ctx *rct_create_slab(int L, int det_w, int det_h, int n_views, int z_first, int z_count) {
     if (L <= 0 || det_w <= 0 || det_h <= 0 || n_views <= 0) {
         fail(RCT_EINVAL, "rct_create: L=%d det_w=%d det_h=%d n_views=%d must be positive", L, det_w, det_h, n_views);
         return nullptr;
     }
     if (L > 2048) {
         fail(RCT_EINVAL, "rct_create: L=%d exceeds 2048", L);
+        return nullptr;
+    }
+    if (z_first < 0 || z_count <= 0 || z_count > L - z_first) {
+        fail(RCT_EINVAL, "rct_create_slab: planes [%d, %lld) are not a non-empty range inside [0, %d)", z_first,
+             (long long)z_first + z_count, L);
         return nullptr;
     }
     int dev = 0;
@@ -600,9 +684,11 @@ rct_ctx *rct_create(int L, int det_w, int det_h, int n_views) {
     c->W = det_w;
     c->H = det_h;
     c->n_views = n_views;
+    c->z_first = z_first;
+    c->z_count = z_count;
     c->device = dev;
     c->tune = default_tuning(L);
-    const size_t bytes = (size_t)L * L * L * sizeof(float);
+    const size_t bytes = (size_t)z_count * L * L * sizeof(float);
     e = cudaMalloc(&c->vol, bytes);
     if (e != cudaSuccess) {
         fail(RCT_ENOMEM, "rct_create: volume allocation of %zu bytes failed (%s)", bytes, cudaGetErrorName(e));
@@ -624,7 +710,7 @@ rct_ctx *rct_create(int L, int det_w, int det_h, int n_views) {
     c->id = g_next_id.fetch_add(1);
     {
         std::lock_guard<std::mutex> lk(g_reg_mu);
-        g_live[c->id] = c->gen;
+        g_live[c->id] = LiveEntry{c->gen, c};
     }
     return c;
 }
@@ -638,7 +724,7 @@ void rct_destroy(rct_ctx *c) {
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
-    cudaDeviceSynchronize();
+    (void)wait_idle(c);
     free_slots(c);
     if (c->vol) cudaFree(c->vol);
     if (c->lin_stage) cudaFree(c->lin_stage);
@@ -657,6 +743,7 @@ void rct_destroy(rct_ctx *c) {
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+    if (c->ev_done) cudaEventDestroy(c->ev_done);
     if (prev >= 0) cudaSetDevice(prev);
     delete c;
 }
@@ -679,8 +766,9 @@ rct_status rct_set_geometry(rct_ctx *c, const double *matrices, const double ori
         }
     }
     // Passes already queued with a previous geometry read the block-frame table when they run:
-    // let them finish before it is overwritten (a fresh context has none).
-    if (c->launches > 0) RCT_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    // let this context's work finish before it is overwritten (a fresh context has none).  Other
+    // contexts' work on the device is not waited for.
+    if (c->launches > 0) RCT_CUDA(wait_idle(c), "waiting for the context's queued work");
     if (c->geometry_set) bump(c);   // graphs captured before read the table in place
     if ((st = ensure_copy_machinery(c))) return st;
     RCT_CUDA(cudaMemcpyAsync(c->geo_dev, geo.data(), sizeof(ViewGeo) * c->n_views, cudaMemcpyHostToDevice,
@@ -748,8 +836,9 @@ rct_status rct_set_filter(rct_ctx *c, double sdd, double pitch, const double *pr
     std::vector<float2> pp(c->n_views);
     for (int v = 0; v < c->n_views; ++v)
         pp[v] = make_float2(static_cast<float>(principal[2 * v]), static_cast<float>(principal[2 * v + 1]));
-    // Filter launches already queued read the old tables: let them finish before they are replaced.
-    RCT_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    // Filter launches already queued read the old tables: let this context's work finish before they
+    // are replaced (other contexts keep running).
+    RCT_CUDA(wait_idle(c), "waiting for the context's queued work");
     if (c->filter_set) bump(c);     // graphs captured before point at the old tables
     if (c->filt_twiddle) cudaFree(c->filt_twiddle);
     if (c->filt_spectrum) cudaFree(c->filt_spectrum);
@@ -806,6 +895,7 @@ rct_status rct_filter_projections(rct_ctx *c, const float *d_raw, void *d_out, i
     f.principal = c->filt_principal + first_view;
     cudaError_t e = launch_ramp_filter(f, d_raw, d_out, out_dtype, n, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "ramp filter launch");
+    RCT_CUDA(mark_done(c, stream), "cudaEventRecord");
     return RCT_OK;
 }
 
@@ -818,7 +908,7 @@ rct_status rct_debug_bound_violations(rct_ctx *c, unsigned long long *count) {
         *count = 0;
         return RCT_OK;
     }
-    RCT_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    RCT_CUDA(wait_idle(c), "waiting for the context's queued work");
     RCT_CUDA(cudaMemcpy(count, c->viol_dev, sizeof *count, cudaMemcpyDeviceToHost), "cudaMemcpy");
     return RCT_OK;
 #else
@@ -891,7 +981,7 @@ rct_status rct_set_tuning(rct_ctx *c, const rct_tuning *t) {
     if (c->L % n.xvec != 0) return fail(RCT_EINVAL, "xvec %d does not divide L = %d", n.xvec, c->L);
     if (n.block_x < 1 || n.block_y < 1 || n.block_x * n.block_y > 512 || (n.block_x * n.block_y) % 32 != 0)
         return fail(RCT_EINVAL, "block %dx%d: need a multiple of 32 threads, at most 512", n.block_x, n.block_y);
-    if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_PAIR) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
+    if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_DQUAD) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
     if (n.tex_zrun < 0 || n.tex_zrun > 16) return fail(RCT_EINVAL, "tex_zrun %d outside 0..16", n.tex_zrun);
     c->tune = n;
     return RCT_OK;
@@ -915,7 +1005,7 @@ rct_status rct_reset_volume(rct_ctx *c, void *stream) {
 
 static rct_status materialise_zero(rct_ctx *c, cudaStream_t s) {
     if (!c->vol_zero_pending) return RCT_OK;
-    RCT_CUDA(cudaMemsetAsync(c->vol, 0, (size_t)c->L * c->L * c->L * sizeof(float), s), "cudaMemsetAsync");
+    RCT_CUDA(cudaMemsetAsync(c->vol, 0, (size_t)c->z_count * c->L * c->L * sizeof(float), s), "cudaMemsetAsync");
     c->vol_zero_pending = false;
     return RCT_OK;
 }
@@ -926,6 +1016,7 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
     note_capture(c, stream);
     if ((st = validate_range(c, d_proj, first_view, n))) return st;
     if (n == 0) return RCT_OK;
+    if ((st = check_route(c))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int kind = kernel_kind(c);
     const int K = c->tune.views_per_pass;
@@ -982,6 +1073,7 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
         c->vol_zero_pending = false;
         if (staged) RCT_CUDA(cudaEventRecord(c->ev_free[g], s), "cudaEventRecord");
     }
+    RCT_CUDA(mark_done(c, stream), "cudaEventRecord");
     return RCT_OK;
 }
 
@@ -997,6 +1089,7 @@ rct_status backproject_host_impl(rct_ctx *c, const void *h_proj, int first_view,
     const int kind = kernel_kind(c);
     const int K = c->tune.views_per_pass;
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
+    if ((st = check_route(c))) return st;
     if ((st = ensure_host_staging(c))) return st;
     const bool tex = uses_tex(c);
     const bool quad = uses_quad(c);
@@ -1045,21 +1138,24 @@ rct_status backproject_host_impl(rct_ctx *c, const void *h_proj, int first_view,
         if (read_dst && b + kb >= n) {
             // last pass: z-slabs of a whole number of z-runs, each copied out when it is done
             const int R = c->tune.zrun;
-            const int slab = ((c->L + kReadSlabs - 1) / kReadSlabs + R - 1) / R * R;
+            const int slab = ((c->z_count + kReadSlabs - 1) / kReadSlabs + R - 1) / R * R;
             const size_t plane = (size_t)c->L * c->L;
+            const int z_end = c->z_first + c->z_count;
             int i = 0;
-            for (int z = 0; z < c->L; z += slab, ++i) {
+            for (int z = c->z_first; z < z_end; z += slab, ++i) {
                 p.z_base = z;
-                p.z_count = std::min(slab, c->L - z);
+                p.z_count = std::min(slab, z_end - z);
                 cudaError_t e = launch(c, lc, p, s);
                 if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
+                const size_t at = (size_t)(z - c->z_first) * plane;
                 RCT_CUDA(cudaEventRecord(c->ev_slab[i], s), "cudaEventRecord");
                 RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_slab[i], 0), "cudaStreamWaitEvent");
-                RCT_CUDA(cudaMemcpyAsync(read_dst + z * plane, c->vol + z * plane, sizeof(float) * plane * p.z_count,
+                RCT_CUDA(cudaMemcpyAsync(read_dst + at, c->vol + at, sizeof(float) * plane * p.z_count,
                                          cudaMemcpyDefault, c->copy_stream),
                          "cudaMemcpyAsync(volume slab)");
             }
-            p.z_base = p.z_count = 0;
+            p.z_base = c->z_first;
+            p.z_count = c->z_count;
             RCT_CUDA(cudaEventRecord(c->ev_slab[i], c->copy_stream), "cudaEventRecord");
             RCT_CUDA(cudaStreamWaitEvent(s, c->ev_slab[i], 0), "cudaStreamWaitEvent");
         } else {
@@ -1069,6 +1165,7 @@ rct_status backproject_host_impl(rct_ctx *c, const void *h_proj, int first_view,
         c->vol_zero_pending = false;
         RCT_CUDA(cudaEventRecord(c->ev_free[g], s), "cudaEventRecord");
     }
+    RCT_CUDA(mark_done(c, stream), "cudaEventRecord");
     return RCT_OK;
 }
 
@@ -1107,8 +1204,9 @@ rct_status rct_read_volume(rct_ctx *c, float *dst, void *stream) {
     if (!dst) return fail(RCT_EINVAL, "null destination");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((st = materialise_zero(c, s))) return st;
-    RCT_CUDA(cudaMemcpyAsync(dst, c->vol, (size_t)c->L * c->L * c->L * sizeof(float), cudaMemcpyDefault, s),
+    RCT_CUDA(cudaMemcpyAsync(dst, c->vol, (size_t)c->z_count * c->L * c->L * sizeof(float), cudaMemcpyDefault, s),
              "cudaMemcpyAsync(volume)");
+    RCT_CUDA(mark_done(c, stream), "cudaEventRecord");
     return RCT_OK;
 }
 
@@ -1118,9 +1216,10 @@ rct_status rct_write_volume(rct_ctx *c, const float *src, void *stream) {
     note_capture(c, stream);
     if (!src) return fail(RCT_EINVAL, "null source");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    RCT_CUDA(cudaMemcpyAsync(c->vol, src, (size_t)c->L * c->L * c->L * sizeof(float), cudaMemcpyDefault, s),
+    RCT_CUDA(cudaMemcpyAsync(c->vol, src, (size_t)c->z_count * c->L * c->L * sizeof(float), cudaMemcpyDefault, s),
              "cudaMemcpyAsync(volume)");
     c->vol_zero_pending = false;
+    RCT_CUDA(mark_done(c, stream), "cudaEventRecord");
     return RCT_OK;
 }
 
@@ -1132,6 +1231,7 @@ float *rct_volume_device_ptr(rct_ctx *c) {
     if (c->vol_zero_pending) {
         // A caller reading the buffer directly must see zeros: materialise on the legacy stream.
         if (materialise_zero(c, nullptr) != RCT_OK) return nullptr;
+        (void)mark_done(c, nullptr);
     }
     return c->vol;
 }
@@ -1145,11 +1245,26 @@ rct_status rct_get_shape(const rct_ctx *c, int *L, int *det_w, int *det_h, int *
     return RCT_OK;
 }
 
+rct_status rct_get_slab(const rct_ctx *c, int *z_first, int *z_count) {
+    if (!c) return fail(RCT_EINVAL, "null context");
+    if (z_first) *z_first = c->z_first;
+    if (z_count) *z_count = c->z_count;
+    return RCT_OK;
+}
+
+rct_status rct_get_precision(const rct_ctx *c, int *proj_dtype, int *interp) {
+    if (!c) return fail(RCT_EINVAL, "null context");
+    if (proj_dtype) *proj_dtype = c->dtype;
+    if (interp) *interp = c->interp;
+    return RCT_OK;
+}
+
 int64_t rct_launch_count(const rct_ctx *c) { return c ? c->launches : -1; }
 
 rct_status rct_prepare(rct_ctx *c, int host_input) {
     rct_status st = check_ctx(c);
     if (st) return st;
+    if ((st = check_route(c))) return st;
     if ((uses_tex(c) || uses_quad(c)) && (st = ensure_copy_machinery(c))) return st;
     if ((st = ensure_slots(c, 2 * c->tune.views_per_pass))) return st;
     if ((st = ensure_quads(c, 2 * c->tune.views_per_pass))) return st;
@@ -1213,18 +1328,22 @@ rct_status rct_graph_end(void *stream, rct_graph **out) {
 
 rct_status rct_graph_launch(rct_graph *g, void *stream) {
     if (!g) return fail(RCT_EINVAL, "null graph");
+    std::vector<rct_ctx *> used;
     {
         std::lock_guard<std::mutex> lk(g_reg_mu);
         for (const auto &u : g->uses) {
             const auto it = g_live.find(u.first);
             if (it == g_live.end())
                 return fail(RCT_ESTATE, "a context this graph was captured with has been destroyed");
-            if (it->second != u.second)
+            if (it->second.gen != u.second)
                 return fail(RCT_ESTATE, "a context this graph was captured with has replaced its staging, "
                                         "geometry table or filter tables since: capture the graph again");
+            used.push_back(it->second.ctx);
         }
     }
     RCT_CUDA(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), "cudaGraphLaunch");
+    // the replay is now the last work of every context it uses
+    for (rct_ctx *c : used) RCT_CUDA(mark_done(c, stream), "cudaEventRecord");
     return RCT_OK;
 }
 

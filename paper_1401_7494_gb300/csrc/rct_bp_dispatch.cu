@@ -12,6 +12,7 @@ namespace rct {
     cudaError_t launch_bp_soft_##dt##_pld(const LaunchConfig &, const BpParams &, cudaStream_t); \
     cudaError_t launch_bp_soft_##dt##_mix(const LaunchConfig &, const BpParams &, cudaStream_t);
 RCT_DECLARE_ROUTES(f32)
+cudaError_t launch_bp_soft_f32_dqd(const LaunchConfig &, const BpParams &, cudaStream_t);
 RCT_DECLARE_ROUTES(f16)
 RCT_DECLARE_ROUTES(bf16)
 #undef RCT_DECLARE_ROUTES
@@ -24,8 +25,17 @@ RCT_DECLARE_ROUTES(bf16)
     if (p.tex_zrun < c.zrun) return launch_bp_soft_##dt##_mix(c, p, s);                           \
     return launch_bp_soft_##dt##_tex(c, p, s);
 
-cudaError_t launch_bp_soft_f32(const LaunchConfig &c, const BpParams &p, cudaStream_t s) { RCT_ROUTE_SWITCH(f32) }
-cudaError_t launch_bp_soft_f16(const LaunchConfig &c, const BpParams &p, cudaStream_t s) { RCT_ROUTE_SWITCH(f16) }
-cudaError_t launch_bp_soft_bf16(const LaunchConfig &c, const BpParams &p, cudaStream_t s) { RCT_ROUTE_SWITCH(bf16) }
+cudaError_t launch_bp_soft_f32(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
+    if (p.tex_zrun <= 0 && p.quad == 3) return launch_bp_soft_f32_dqd(c, p, s);
+    RCT_ROUTE_SWITCH(f32)
+}
+cudaError_t launch_bp_soft_f16(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
+    if (p.quad == 3) return cudaErrorInvalidValue;   // difference quads hold FP32 values
+    RCT_ROUTE_SWITCH(f16)
+}
+cudaError_t launch_bp_soft_bf16(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
+    if (p.quad == 3) return cudaErrorInvalidValue;
+    RCT_ROUTE_SWITCH(bf16)
+}
 
 }  // namespace rct

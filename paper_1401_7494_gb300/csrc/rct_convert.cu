@@ -124,7 +124,25 @@ __global__ void stage_pairs_u16(const unsigned short *__restrict__ img, unsigned
     q[static_cast<size_t>(jy) * (W + 2) + ix] = a | (c << 16);
 }
 
+// One thread per padded element (jy, ix): the cell with corner (ix - 1, jy - 1) as (a, c, b - a, d - c),
+// a = I[j0][i0], c = I[j0+1][i0], b = I[j0][i0+1], d = I[j0+1][i0+1], zero off the image.
+__global__ void stage_dquads_f32(const float *__restrict__ img, float4 *__restrict__ q, int W, int H) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jy = blockIdx.y;
+    if (ix > W) return;
+    const int i0 = ix - 1, j0 = jy - 1;
+    const float a = px_or_zero(img, W, H, i0, j0), c = px_or_zero(img, W, H, i0, j0 + 1);
+    const float b = px_or_zero(img, W, H, i0 + 1, j0), d = px_or_zero(img, W, H, i0 + 1, j0 + 1);
+    q[static_cast<size_t>(jy) * (W + 1) + ix] = make_float4(a, c, __fsub_rn(b, a), __fsub_rn(d, c));
+}
+
 }  // namespace
+
+cudaError_t launch_stage_dquads(const float *src, void *dst, int W, int H, cudaStream_t s) {
+    const dim3 block(256), grid((W + 1 + 255) / 256, H + 1);
+    stage_dquads_f32<<<grid, block, 0, s>>>(src, static_cast<float4 *>(dst), W, H);
+    return cudaGetLastError();
+}
 
 size_t pair_bytes(int W, int H, int dtype) {
     return static_cast<size_t>(W + 2) * (H + 1) * (dtype == DT_F32 ? 8 : 4);

@@ -55,22 +55,30 @@ struct __align__(16) ViewGeo {
 // 8 bytes FP16/BF16).  A pair element at padded (row jy, column ix) holds the vertical pair
 // (I[jy-1][ix-1], I[jy][ix-1]); the pair image has H + 1 rows of W + 2 pairs (8 bytes FP32,
 // 4 bytes FP16/BF16), and the cell with corner (i0, j0) is the two consecutive pairs at
-// (j0 + 1, i0 + 1) and (j0 + 1, i0 + 2).  A cell with a tap on the image has its padded index in
+// (j0 + 1, i0 + 1) and (j0 + 1, i0 + 2).  A difference quad (FP32 only) is laid out as a quad
+// element, H + 1 rows of W + 1 elements of 16 bytes, but holds (I[j0][i0], I[j0+1][i0],
+// I[j0][i0+1] - I[j0][i0], I[j0+1][i0+1] - I[j0+1][i0]), the differences rounded to FP32: the
+// horizontal lerps of both rows are then one packed FMA, with the very roundings the quad and pair
+// routes perform in the kernel.  A cell with a tap on the image has its padded index in
 // [0, W] x [0, H]; a kernel tests that and sends every other lane to element 0.
 
 struct BpParams {
-    float *vol;      // L^3, z-major, x fastest
+    float *vol;      // planes [vol_z0, vol_z0 + planes held) of the L^3 volume, z-major, x fastest
+    int vol_z0;      // z plane of vol[0] (0 for a whole-volume context; z_first of a slab context)
     int L, W, H;
     int K;           // views in this pass, 1..KMAX
     float cen;       // (L - 1) / 2
     int accumulate;  // 0: the volume is logically zero, overwrite instead of adding
     int tex_zrun;    // G_SOFT: z positions [0, tex_zrun) of each run use the texture gather
-    int quad;        // G_SOFT load route: 0 = linear image, 1 = staged quads, 2 = staged pairs
+    int quad;        // G_SOFT load route: 0 = linear image, 1 = staged quads, 2 = staged pairs,
+                     // 3 = staged difference quads
     const ViewGeo *geo;  // G_SOFT: the context's per-view geometry for block frames (null: global frame)
     int first_view;      // view index of view[0] in geo
     int z_base;          // first z plane of this launch (0: the whole volume)
-    int z_count;         // z planes from z_base (0: all L); a multiple of the z-run unless it ends at L
+    int z_count;         // z planes from z_base (0: up to L); the launch writes no plane at or past
+                         // z_base + z_count
     long long qelems;    // elements of one staged quad / pair image (bounds-checking build only)
+    long long vol_elems; // floats held at vol (bounds-checking build only)
     unsigned long long *viol;  // bounds-checking build: violation counter on the device (null: not counted)
     ViewParams view[KMAX];
 };
@@ -110,6 +118,8 @@ cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dty
 size_t quad_bytes(int W, int H, int dtype);
 // Build the zero-padded vertical-pair image of one view (see ViewParams).
 cudaError_t launch_stage_pairs(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s);
+// Build the zero-padded difference-quad image of one FP32 view (see ViewParams); quad_bytes(W, H, DT_F32).
+cudaError_t launch_stage_dquads(const float *src, void *dst, int W, int H, cudaStream_t s);
 size_t pair_bytes(int W, int H, int dtype);
 
 // Fill the matrix of a view (FP32) from its FP64 fold (rows u', v', w over centred voxel

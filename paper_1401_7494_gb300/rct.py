@@ -22,7 +22,7 @@ RCT_PROJ_F32, RCT_PROJ_F16, RCT_PROJ_BF16 = 0, 1, 2
 RCT_INTERP_SOFT, RCT_INTERP_TEX = 0, 1
 RCT_FRAME_GLOBAL, RCT_FRAME_BLOCK = 0, 1
 RCT_INDEX_FLOOR, RCT_INDEX_TRUNC = 0, 1
-RCT_GATHER_AUTO, RCT_GATHER_LDG, RCT_GATHER_TLD4, RCT_GATHER_MIX, RCT_GATHER_QUAD, RCT_GATHER_PAIR = 0, 1, 2, 3, 4, 5
+RCT_GATHER_AUTO, RCT_GATHER_LDG, RCT_GATHER_TLD4, RCT_GATHER_MIX, RCT_GATHER_QUAD, RCT_GATHER_PAIR, RCT_GATHER_DQUAD = range(7)
 RCT_MAX_VIEWS_PER_PASS = 32
 STATUS_NAMES = {0: "RCT_OK", 1: "RCT_EINVAL", 2: "RCT_ENOMEM", 3: "RCT_ECUDA", 4: "RCT_ESTATE",
                 5: "RCT_ETIMEOUT", 6: "RCT_ENOTSUP"}
@@ -51,6 +51,9 @@ _I = ctypes.c_int
 _D3 = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "rct_create": (_P, [_I, _I, _I, _I]),
+    "rct_create_slab": (_P, [_I, _I, _I, _I, _I, _I]),
+    "rct_get_slab": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "rct_get_precision": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "rct_destroy": (None, [_P]),
     "rct_set_geometry": (_I, [_P, _D3, _D3, _D3]),
     "rct_set_precision": (_I, [_P, _I, _I]),
@@ -84,8 +87,6 @@ SIGNATURES = {
     "rct_graph_end": (_I, [_P, ctypes.POINTER(_P)]),
     "rct_graph_launch": (_I, [_P, _P]),
     "rct_graph_destroy": (None, [_P]),
-    "rct_probe_texture": (_I, [_I, _I, ctypes.c_float, ctypes.c_float, _I, ctypes.POINTER(ctypes.c_double)]),
-    "rct_probe_update_stream": (_I, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]),
     "rct_backproject_f16_noalloc": (_I, [_I, _I, _I, _D3, _I, _D3, _D3, _P, _P, _I, _P]),
     "rct_last_error": (ctypes.c_char_p, []),
     "rct_version": (_I, []),
@@ -133,6 +134,62 @@ def _addr(buf) -> int | None:
     raise TypeError(f"cannot take the address of {type(buf).__name__}")
 
 
+_ELEM = {RCT_PROJ_F32: 4, RCT_PROJ_F16: 2, RCT_PROJ_BF16: 2}
+
+
+def _torch_dtypes(code: int):
+    import torch
+    return {RCT_PROJ_F32: (torch.float32,), RCT_PROJ_F16: (torch.float16,),
+            RCT_PROJ_BF16: (torch.bfloat16,)}[code]
+
+
+def _np_dtypes(code: int):
+    return {RCT_PROJ_F32: (np.float32,), RCT_PROJ_F16: (np.float16,), RCT_PROJ_BF16: ()}[code]
+
+
+def _check_buffer(buf, what: str, *, code: int, min_elems: int, where: str) -> None:
+    """Validate a tensor or array before its address goes to the library: its element type (the
+    rct_proj_dtype ``code``), its size (at least ``min_elems`` elements) and where it lives
+    (``where`` = "device": a CUDA tensor on the current device; "host": host memory; "any": either).
+    Raw integer addresses cannot be checked and are passed through.  Raises ValueError."""
+    if buf is None or isinstance(buf, int):
+        return
+    if hasattr(buf, "data_ptr") and hasattr(buf, "dtype"):
+        import torch
+        if buf.dtype not in _torch_dtypes(code):
+            raise ValueError(f"{what}: dtype {buf.dtype} where {_torch_dtypes(code)[0]} is expected")
+        if buf.is_cuda:
+            if where == "host":
+                raise ValueError(f"{what}: a host buffer is expected, got a tensor on {buf.device}")
+            cur = torch.cuda.current_device()
+            if buf.device.index != cur:
+                raise ValueError(f"{what}: tensor on {buf.device} but cuda:{cur} is the current device")
+        else:
+            if where == "device":
+                raise ValueError(f"{what}: a CUDA tensor is expected, got one on {buf.device}")
+            if buf.device.type != "cpu":
+                raise ValueError(f"{what}: tensors on {buf.device} cannot be passed")
+        n = buf.numel()
+    elif isinstance(buf, np.ndarray):
+        if where == "device":
+            raise ValueError(f"{what}: a CUDA tensor is expected, got a numpy array")
+        if buf.dtype.type not in _np_dtypes(code) and not (code == RCT_PROJ_BF16 and buf.dtype == np.uint16):
+            raise ValueError(f"{what}: dtype {buf.dtype} does not match the storage type")
+        n = buf.size
+    else:
+        return
+    if n < min_elems:
+        raise ValueError(f"{what}: {n} elements, at least {min_elems} needed")
+
+
+def _ctx_sizes(ctx) -> tuple[int, int, int, int, int, int]:
+    """(L, det_w, det_h, planes held, proj dtype code, interp) of a context."""
+    L, W, H, _ = rct_get_shape(ctx)
+    _, zc = rct_get_slab(ctx)
+    dt, it = rct_get_precision(ctx)
+    return L, W, H, zc, dt, it
+
+
 def _stream(stream) -> int | None:
     if stream is None:
         return None
@@ -163,6 +220,25 @@ def rct_create(L: int, det_w: int, det_h: int, n_views: int) -> int:
     if not h:
         raise RctError(RCT_EINVAL, rct_last_error())
     return h
+
+
+def rct_create_slab(L: int, det_w: int, det_h: int, n_views: int, z_first: int, z_count: int) -> int:
+    h = lib().rct_create_slab(L, det_w, det_h, n_views, z_first, z_count)
+    if not h:
+        raise RctError(RCT_EINVAL, rct_last_error())
+    return h
+
+
+def rct_get_slab(ctx) -> tuple[int, int]:
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().rct_get_slab(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def rct_get_precision(ctx) -> tuple[int, int]:
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().rct_get_precision(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def rct_destroy(ctx) -> None:
@@ -201,6 +277,11 @@ def rct_set_filter(ctx, sdd: float, pitch: float, principal) -> None:
 
 
 def rct_filter_projections(ctx, d_raw, d_out, out_dtype: int, first_view: int, n: int, stream=None) -> None:
+    if not isinstance(d_raw, int) or not isinstance(d_out, int):
+        _, W, H, _, _, _ = _ctx_sizes(ctx)
+        _check_buffer(d_raw, "d_raw", code=RCT_PROJ_F32, min_elems=max(n, 0) * W * H, where="device")
+        if out_dtype in _ELEM:
+            _check_buffer(d_out, "d_out", code=int(out_dtype), min_elems=max(n, 0) * W * H, where="device")
     _check(lib().rct_filter_projections(ctx, _addr(d_raw), _addr(d_out), int(out_dtype), first_view, n,
                                         _stream(stream)))
 
@@ -248,23 +329,43 @@ def rct_reset_volume(ctx, stream=None) -> None:
     _check(lib().rct_reset_volume(ctx, _stream(stream)))
 
 
+def _check_proj(ctx, proj, n: int, where: str) -> None:
+    if proj is None or isinstance(proj, int):
+        return
+    _, W, H, _, dt, _ = _ctx_sizes(ctx)
+    _check_buffer(proj, "projections", code=dt, min_elems=max(n, 0) * W * H, where=where)
+
+
+def _check_volume(ctx, vol, what: str, where: str = "any") -> None:
+    if vol is None or isinstance(vol, int):
+        return
+    L, _, _, zc, _, _ = _ctx_sizes(ctx)
+    _check_buffer(vol, what, code=RCT_PROJ_F32, min_elems=zc * L * L, where=where)
+
+
 def rct_backproject(ctx, d_proj, first_view: int, n: int, stream=None) -> None:
+    _check_proj(ctx, d_proj, n, "device")
     _check(lib().rct_backproject(ctx, _addr(d_proj), first_view, n, _stream(stream)))
 
 
 def rct_backproject_host(ctx, h_proj, first_view: int, n: int, stream=None) -> None:
+    _check_proj(ctx, h_proj, n, "host")
     _check(lib().rct_backproject_host(ctx, _addr(h_proj), first_view, n, _stream(stream)))
 
 
 def rct_backproject_host_read(ctx, h_proj, first_view: int, n: int, dst, stream=None) -> None:
+    _check_proj(ctx, h_proj, n, "host")
+    _check_volume(ctx, dst, "dst")
     _check(lib().rct_backproject_host_read(ctx, _addr(h_proj), first_view, n, _addr(dst), _stream(stream)))
 
 
 def rct_read_volume(ctx, dst, stream=None) -> None:
+    _check_volume(ctx, dst, "dst")
     _check(lib().rct_read_volume(ctx, _addr(dst), _stream(stream)))
 
 
 def rct_write_volume(ctx, src, stream=None) -> None:
+    _check_volume(ctx, src, "src")
     _check(lib().rct_write_volume(ctx, _addr(src), _stream(stream)))
 
 
@@ -297,6 +398,9 @@ def rct_profile_read(ctx) -> tuple[float, int]:
 
 
 def rct_convert_projections(d_src, d_dst, n: int, dtype: int, stream=None) -> None:
+    _check_buffer(d_src, "d_src", code=RCT_PROJ_F32, min_elems=n, where="device")
+    if dtype in _ELEM:
+        _check_buffer(d_dst, "d_dst", code=int(dtype), min_elems=n, where="device")
     _check(lib().rct_convert_projections(_addr(d_src), _addr(d_dst), n, dtype, _stream(stream)))
 
 
@@ -328,24 +432,14 @@ def rct_graph_destroy(graph) -> None:
         lib().rct_graph_destroy(graph)
 
 
-def rct_probe_texture(mode: int, dtype: int, stride_px: float, step_px: float, iters: int = 4096) -> float:
-    r = ctypes.c_double()
-    _check(lib().rct_probe_texture(mode, dtype, stride_px, step_px, iters, ctypes.byref(r)))
-    return r.value
-
-
-def rct_probe_update_stream(nbytes: int) -> float:
-    r = ctypes.c_double()
-    _check(lib().rct_probe_update_stream(nbytes, ctypes.byref(r)))
-    return r.value
-
-
 def rct_backproject_f16_noalloc(L: int, det_w: int, det_h: int, matrices, origin, spacing, d_proj, n: int,
                                 d_volume, accumulate: bool = False, stream=None) -> None:
     """Allocation-free FP16-storage backprojection into a caller-owned volume (see include/rct.h)."""
     m = np.ascontiguousarray(np.asarray(matrices, dtype=np.float64).reshape(-1))
     if m.size < 12 * n:
         raise ValueError("matrices must hold 12 values per view")
+    _check_buffer(d_proj, "d_proj", code=RCT_PROJ_F32, min_elems=max(n, 0) * det_w * det_h, where="device")
+    _check_buffer(d_volume, "d_volume", code=RCT_PROJ_F32, min_elems=L ** 3, where="device")
     o, po = _f64(origin, 3)
     s, ps = _f64(spacing, 3)
     _check(lib().rct_backproject_f16_noalloc(L, det_w, det_h, m.ctypes.data_as(_D3), n, po, ps, _addr(d_proj),
@@ -369,14 +463,19 @@ def rct_fold_geometry(L: int, matrices, origin, spacing):
 
 @dataclass
 class Backprojector:
-    """Owns one context: an L^3 FP32 volume on the current device and a scan geometry."""
+    """Owns one context: an L^3 FP32 volume on the current device and a scan geometry.  With
+    ``z_range=(z_first, z_count)`` the context holds only those z planes (rct_create_slab)."""
     L: int
     det_w: int
     det_h: int
     n_views: int
+    z_range: tuple | None = None
 
     def __post_init__(self):
-        self.ctx = rct_create(self.L, self.det_w, self.det_h, self.n_views)
+        if self.z_range is None:
+            self.ctx = rct_create(self.L, self.det_w, self.det_h, self.n_views)
+        else:
+            self.ctx = rct_create_slab(self.L, self.det_w, self.det_h, self.n_views, *self.z_range)
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -107,8 +107,10 @@ def test_filter_argument_errors(cuda_device):
                 bp.set_filter(sdd, pitch, w.geom.principal)
             assert e.value.status == rct.RCT_EINVAL
         bp.set_filter(w.geom.sdd, w.geom.pitch, w.geom.principal)
-        with pytest.raises(rct.RctError) as e:                       # 16-bit output over its own input
+        with pytest.raises(ValueError):                              # the binding checks a tensor's type
             rct.rct_filter_projections(bp.ctx, raw, raw, rct.RCT_PROJ_F16, 0, w.n_views, None)
+        with pytest.raises(rct.RctError) as e:                       # 16-bit output over its own input
+            rct.rct_filter_projections(bp.ctx, raw.data_ptr(), raw.data_ptr(), rct.RCT_PROJ_F16, 0, w.n_views, None)
         assert e.value.status == rct.RCT_EINVAL
         with pytest.raises(rct.RctError) as e:                       # partial overlap
             rct.rct_filter_projections(bp.ctx, raw, raw[1:], rct.RCT_PROJ_F32, 0, 2, None)

@@ -44,6 +44,9 @@ TUNINGS = [
     dict(gather=rct.RCT_GATHER_PAIR, views_per_pass=11, zrun=1, xvec=2, block_x=32, block_y=2),
     dict(gather=rct.RCT_GATHER_PAIR, views_per_pass=16, zrun=16, xvec=1, block_x=8, block_y=16),
     dict(gather=rct.RCT_GATHER_TLD4, views_per_pass=8, zrun=16, xvec=2, block_x=16, block_y=8),
+    dict(gather=rct.RCT_GATHER_DQUAD, views_per_pass=24, zrun=8, xvec=1, block_x=8, block_y=16),
+    dict(gather=rct.RCT_GATHER_DQUAD, views_per_pass=7, zrun=16, xvec=2, block_x=16, block_y=8),
+    dict(gather=rct.RCT_GATHER_DQUAD, views_per_pass=13, zrun=2, xvec=4, block_x=8, block_y=8),
 ]
 
 
@@ -189,7 +192,7 @@ def test_argument_errors(cuda_device):
         with pytest.raises(rct.RctError):
             rct.rct_backproject(bp.ctx, 0, 0, 2, None)
         for bad in [dict(views_per_pass=33), dict(zrun=3), dict(zrun=16, xvec=4), dict(xvec=3), dict(block_x=7, block_y=1),
-                    dict(block_x=1024, block_y=1), dict(gather=9), dict(gather=6), dict(tex_zrun=17)]:
+                    dict(block_x=1024, block_y=1), dict(gather=9), dict(gather=7), dict(tex_zrun=17)]:
             with pytest.raises(rct.RctError):
                 bp.set_tuning(**bad)
         with pytest.raises(rct.RctError):
@@ -501,3 +504,28 @@ def test_graph_replay_of_the_host_input_step_is_bitwise_the_direct_call(small_ca
                     assert torch.equal(replayed, direct), tun
             finally:
                 rct.rct_graph_destroy(g)
+
+
+@pytest.mark.parametrize("zrun,xvec", [(8, 1), (16, 2), (1, 4)])
+def test_staged_routes_are_bitwise_equal(small_cases, zrun, xvec):
+    """Quads, pairs and difference quads feed the same roundings to the same sums, on the fast path
+    (warps wholly on the image) and off it: their volumes are identical, and so are the plain loads'."""
+    w, proj, host = small_cases["L64"]
+    base = dict(views_per_pass=12, zrun=zrun, xvec=xvec, block_x=8, block_y=16)
+    vols = {g: gpu_backproject(w, proj, tuning=dict(base, gather=g))
+            for g in (rct.RCT_GATHER_PAIR, rct.RCT_GATHER_QUAD, rct.RCT_GATHER_DQUAD, rct.RCT_GATHER_LDG)}
+    ref = vols[rct.RCT_GATHER_PAIR]
+    for g, v in vols.items():
+        assert np.array_equal(v, ref), f"gather {g} differs from pairs"
+    assert_parity(ref, oracle_volume(w, host), f"staged routes z-run {zrun} x-vector {xvec}")
+
+
+def test_difference_quads_need_fp32(small_cases):
+    w, proj, _ = small_cases["L37"]
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
+        bp.set_precision(rct.RCT_PROJ_F16).set_tuning(gather=rct.RCT_GATHER_DQUAD)
+        data = torch.empty(proj.shape, dtype=torch.float16, device=proj.device)
+        with pytest.raises(rct.RctError) as e:
+            bp.backproject(data, 0, w.n_views)
+        assert e.value.status == rct.RCT_ENOTSUP
