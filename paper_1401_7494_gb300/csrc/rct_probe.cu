@@ -7,13 +7,15 @@
 // as the fetch results need to stay live.  Result: fetches per second over the whole GPU.
 // rct_probe_update_stream: a read-modify-write stream over a large buffer (the paper's
 // "Node Update" benchmark, Table 1): bytes read + written per second.
+// rct_probe_l1_bandwidth: coalesced 16-byte loads that hit L1: the load data path's bytes per second.
+// This file builds the measurement library librct_bench.so (include/rct_bench.h), not librct.so.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <cstdio>
 
-#include "../../include/rct.h"
+#include "../../include/rct_bench.h"
 
 namespace {
 
@@ -106,6 +108,44 @@ __global__ void update_stream_kernel(float4 *__restrict__ a, size_t n4, float s)
     }
 }
 
+// Every block reads its own 16 KiB block of `buf` over and over with coalesced 16-byte loads (a
+// warp's load covers 512 contiguous bytes; the block's eight warps start 2 KiB apart), so after
+// the first pass every load hits L1 (eight resident blocks hold 128 KiB per SM).  The loaded
+// words are folded with XORs (two three-input logic operations per load) into a sink.
+constexpr int kL1Block = 16 * 1024;
+
+__global__ void __launch_bounds__(256) l1_probe_kernel(const uint4 *__restrict__ buf, int iters, unsigned *sink) {
+    const uint4 *base = buf + static_cast<size_t>(blockIdx.x) * (kL1Block / 16);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int at = warp * 128 + lane;                        // in 16-byte units; 1024 units per block
+    unsigned x = 0;
+#pragma unroll 8
+    for (int i = 0; i < iters; ++i) {
+        const uint4 v = __ldg(base + at);
+        x ^= v.x ^ v.y ^ v.z ^ v.w;
+        at = (at + 32) & (kL1Block / 16 - 1);
+    }
+    if (x == 0x9e3779b9u) sink[0] = x;                 // keeps the loads live; practically never taken
+}
+
+// Scattered sector loads served by L2: every lane walks its own pseudo-random sequence of 32-byte
+// sectors of a 64 MiB buffer (far larger than L1, well inside L2) and loads 16 bytes from each with an
+// L1-bypassing load, so each load of a warp asks L2 for 32 distinct sectors.
+constexpr size_t kL2Bytes = size_t(64) << 20;
+
+__global__ void __launch_bounds__(256) l2_sector_probe_kernel(const uint4 *__restrict__ buf, int iters, unsigned *sink) {
+    unsigned s = 2654435761u * (blockIdx.x * blockDim.x + threadIdx.x + 1);
+    unsigned x = 0;
+    constexpr unsigned kSectors = static_cast<unsigned>(kL2Bytes / 32);
+#pragma unroll 8
+    for (int i = 0; i < iters; ++i) {
+        s = s * 1664525u + 1013904223u;                     // LCG: a new sector per load
+        const uint4 v = __ldcg(buf + 2 * static_cast<size_t>(s % kSectors));
+        x ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+    if (x == 0x9e3779b9u) sink[0] = x;
+}
+
 }  // namespace
 
 extern "C" {
@@ -176,6 +216,82 @@ RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float
     if (e1) cudaEventDestroy(e1);
     if (tex) cudaDestroyTextureObject(tex);
     if (arr) cudaFreeArray(arr);
+    if (sink) cudaFree(sink);
+    return st;
+}
+
+RCT_API rct_status rct_probe_l1_bandwidth(int iters, double *rate) {
+    if (!rate || iters < 64) return RCT_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RCT_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int block = 256, grid = sms * 8;
+    uint4 *buf = nullptr;
+    unsigned *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rct_status st = RCT_ECUDA;
+    do {
+        if (cudaMalloc(&buf, static_cast<size_t>(grid) * kL1Block) != cudaSuccess) { st = RCT_ENOMEM; break; }
+        if (cudaMalloc(&sink, sizeof(unsigned)) != cudaSuccess) { st = RCT_ENOMEM; break; }
+        if (cudaMemset(buf, 1, static_cast<size_t>(grid) * kL1Block) != cudaSuccess) break;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) break;
+        l1_probe_kernel<<<grid, block>>>(buf, iters, sink);
+        if (cudaDeviceSynchronize() != cudaSuccess) break;
+        float best = 1e30f;
+        for (int r = 0; r < 5; ++r) {
+            cudaEventRecord(e0);
+            l1_probe_kernel<<<grid, block>>>(buf, iters, sink);
+            cudaEventRecord(e1);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = ms < best ? ms : best;
+        }
+        if (best >= 1e29f) break;
+        *rate = static_cast<double>(grid) * block * iters * 16.0 / (best * 1e-3);
+        st = RCT_OK;
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (buf) cudaFree(buf);
+    if (sink) cudaFree(sink);
+    return st;
+}
+
+RCT_API rct_status rct_probe_l2_sectors(int iters, double *rate) {
+    if (!rate || iters < 64) return RCT_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RCT_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int block = 256, grid = sms * 8;
+    uint4 *buf = nullptr;
+    unsigned *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rct_status st = RCT_ECUDA;
+    do {
+        if (cudaMalloc(&buf, kL2Bytes) != cudaSuccess) { st = RCT_ENOMEM; break; }
+        if (cudaMalloc(&sink, sizeof(unsigned)) != cudaSuccess) { st = RCT_ENOMEM; break; }
+        if (cudaMemset(buf, 1, kL2Bytes) != cudaSuccess) break;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) break;
+        l2_sector_probe_kernel<<<grid, block>>>(buf, iters, sink);
+        if (cudaDeviceSynchronize() != cudaSuccess) break;
+        float best = 1e30f;
+        for (int r = 0; r < 5; ++r) {
+            cudaEventRecord(e0);
+            l2_sector_probe_kernel<<<grid, block>>>(buf, iters, sink);
+            cudaEventRecord(e1);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = ms < best ? ms : best;
+        }
+        if (best >= 1e29f) break;
+        *rate = static_cast<double>(grid) * block * iters / (best * 1e-3);
+        st = RCT_OK;
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (buf) cudaFree(buf);
     if (sink) cudaFree(sink);
     return st;
 }

@@ -13,25 +13,43 @@ from paper_1401_7494_gb300 import build as pkg_build
 ROOT = Path(__file__).resolve().parents[1]
 
 
-def declared_symbols():
+def declared_symbols(*headers):
     names = set()
-    for h in (ROOT / "include").glob("*.h"):
-        text = h.read_text()
+    for name in headers:
+        text = (ROOT / "include" / name).read_text()
         names |= set(re.findall(r"^RCT_API\s+[\w\s\*]*?\b(rct_\w+)\s*\(", text, flags=re.M))
     return names
 
 
-def test_every_declared_symbol_is_exported():
-    decl = declared_symbols()
-    assert {"rct_create", "rct_backproject", "rct_set_geometry", "rct_read_volume"} <= decl
-    lib = rct.lib()
-    out = subprocess.run(["nm", "-D", "--defined-only", str(pkg_build.LIB)], capture_output=True, text=True,
+def exported(path):
+    out = subprocess.run(["nm", "-D", "--defined-only", str(path)], capture_output=True, text=True,
                          check=True).stdout
-    exported = set(re.findall(r"\bT (rct_\w+)$", out, flags=re.M))
-    assert decl <= exported, f"declared but not exported: {sorted(decl - exported)}"
+    return set(re.findall(r"\bT (rct_\w+)$", out, flags=re.M))
+
+
+def test_every_header_is_covered():
+    assert sorted(p.name for p in (ROOT / "include").glob("*.h")) == ["rct.h", "rct_bench.h", "rct_debug.h"]
+
+
+def test_every_declared_symbol_is_exported():
+    decl = declared_symbols("rct.h", "rct_debug.h")
+    assert {"rct_create", "rct_backproject", "rct_set_geometry", "rct_read_volume", "rct_create_slab"} <= decl
+    lib = rct.lib()
+    exp = exported(pkg_build.LIB)
+    assert decl <= exp, f"declared but not exported: {sorted(decl - exp)}"
+    assert not {n for n in exp if n.startswith("rct_probe")}, "probes belong to the measurement library"
     for name in decl:
         assert hasattr(lib, name)
     assert set(rct.SIGNATURES) == decl, "binding and header disagree"
+
+
+def test_measurement_library_exports_the_probes():
+    from paper_1401_7494_gb300 import probes
+    decl = declared_symbols("rct_bench.h")
+    assert decl == {"rct_probe_texture", "rct_probe_update_stream", "rct_probe_l1_bandwidth", "rct_probe_l2_sectors"}
+    probes.lib()
+    assert decl <= exported(pkg_build.BENCH_LIB)
+    assert set(probes.SIGNATURES) == decl
 
 
 def test_version_and_error_channel():
