@@ -33,16 +33,40 @@ METRIC = "GUPS (voxel updates/s) at 512^3 x 496, FP32 projections"
 METRIC_BY_DTYPE = {"f32": METRIC, "f16": METRIC.replace("FP32", "FP16"), "bf16": METRIC.replace("FP32", "BF16")}
 UNIT = "GUPS"
 
-# DRAM bytes (read + write) of one accumulating backprojection pass (L = 512, 1248x960 views) from an ncu
-# capture of that launch, keyed by storage type and the tuning it ran with; a changed kernel or tuning has no
-# entry (traffic reported as null).  Sources: profiles/bp_kernel_pair_f32_L512_ncu_full.md (FP32, pair route)
-# and profiles/bp_kernel_tld4_f16_L512_ncu_full.md (FP16, tld4 route).
-TRAFFIC: dict = {
-    'f32 {"block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0, "views_per_pass": 24, "xvec": 1, "zrun": 8}':
-        787_004_672 + 482_297_600,
-    'f16 {"block_x": 8, "block_y": 16, "gather": 2, "tex_zrun": 0, "views_per_pass": 16, "xvec": 1, "zrun": 8}':
-        576_451_072 + 482_307_840,
-}
+# DRAM bytes (read + write) of one accumulating backprojection pass come from the ncu summaries under
+# profiles/: each capture that measured them carries one line
+#   traffic-record: {"dtype": ..., "tuning": {...}, "kernel_source": <sha256 prefix>, "bytes": ...}
+# and a record counts only for the same storage type, the same tuning and the same kernel source (the
+# hash of the kernel's header files), so a changed kernel or tuning reports traffic as null.
+KERNEL_SOURCES = ("paper_1401_7494_gb300/csrc/rct_bp_kernel.cuh", "paper_1401_7494_gb300/csrc/rct_internal.h")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        h.update((ROOT / rel).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def traffic_records() -> list:
+    out = []
+    for md in sorted((ROOT / "profiles").glob("*.md")):
+        for line in md.read_text().splitlines():
+            if line.startswith("traffic-record:"):
+                rec = json.loads(line.split(":", 1)[1])
+                rec["source"] = md.name
+                out.append(rec)
+    return out
+
+
+def recorded_traffic(dtype: str, tun: dict):
+    """(bytes per accumulating launch, summary file) recorded for this kernel source and tuning, else (None, None)."""
+    src = kernel_source_hash()
+    for rec in traffic_records():
+        if rec.get("dtype") == dtype and rec.get("tuning") == tun and rec.get("kernel_source") == src:
+            return int(rec["bytes"]), rec["source"]
+    return None, None
 
 
 def parse_args():
@@ -54,6 +78,8 @@ def parse_args():
     ap.add_argument("--workload", default="fp32_L512")
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32",
                     help="storage type of the projections for the timed step (FP32 is the headline)")
+    ap.add_argument("--tuning", default=None,
+                    help="JSON object of rct_tuning fields that override the tuning cache for the timed step")
     ap.add_argument("--no-variants", action="store_true", help="skip the precision variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -405,7 +431,7 @@ def k_sweep(dev, stream, peaks: dict) -> dict:
 def run_ours(args, dist: Dist) -> dict | None:
     import torch
     import synth
-    from paper_1401_7494_gb300 import rct, tuning
+    from paper_1401_7494_gb300 import probes, rct, tuning
 
     if dist.world > 1:
         # the per-GPU characterisation legs (variants, pre-filter, K sweep, serving, CPU baseline) describe one
@@ -425,6 +451,8 @@ def run_ours(args, dist: Dist) -> dict | None:
         rct.rct_convert_projections(proj, data, proj.numel(), codes[args.dtype], stream)
     torch.cuda.synchronize()
     tun = tuning.lookup(w.L, args.dtype, "soft")
+    if args.tuning:
+        tun = dict(tun, **json.loads(args.tuning))
     bp = rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views)
     bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_precision(codes[args.dtype], rct.RCT_INTERP_SOFT)
     bp.set_tuning(**tun)
@@ -476,7 +504,7 @@ def run_ours(args, dist: Dist) -> dict | None:
     route = {rct.RCT_GATHER_LDG: "ldg", rct.RCT_GATHER_MIX: "mix", rct.RCT_GATHER_QUAD: "qld",
              rct.RCT_GATHER_PAIR: "pld"}.get(tun.get("gather"), "tex")
     probe = lambda mode, code=rct.RCT_PROJ_F32: round(
-        rct.rct_probe_texture(mode, code, px_per_voxel, px_per_voxel, 4096) / 1e9, 1)
+        probes.rct_probe_texture(mode, code, px_per_voxel, px_per_voxel, 4096) / 1e9, 1)
     probes = {"tex_tld4": probe(0), "ldg4": probe(3), "quad": probe(4), "pair": probe(5)}
     texel = 4 if args.dtype == "f32" else 2
     # The gather needs four texels (16 B FP32, 8 B 16-bit) per update from the L1/texture path.  Its
@@ -492,8 +520,7 @@ def run_ours(args, dist: Dist) -> dict | None:
     bytes_per_launch = bytes_per_step / passes_per_step
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved_gbs = bytes_per_launch / avg_kernel_s / 1e9
-    traffic = (TRAFFIC.get(f"{args.dtype} {json.dumps(tun, sort_keys=True)}")
-               if w.L == 512 and w.n_views == 496 else None)
+    traffic, traffic_src = (recorded_traffic(args.dtype, tun) if w.L == 512 and w.n_views == 496 else (None, None))
     # texture route: one tld4 gather per voxel update against the gather rate the probe measures for the
     # storage type of the step (the texture unit, not the load/store data path, fetches these cells)
     live = live_warp_fraction(w, tun)
@@ -513,6 +540,9 @@ def run_ours(args, dist: Dist) -> dict | None:
     issue_peak_gups = 4 * 32 * sms * sm_mhz * 1e6 / 20.0 / 1e9
     roofline = {"bound": "l1tex", "achieved": round(gather_gbs, 1), "peak": round(l1_peak, 1), "unit": "GB/s",
                 "frac": round(gather_gbs / l1_peak, 4), "traffic": traffic,
+                "traffic_source": (f"profiles/{traffic_src}: dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                   "accumulating launch of this kernel source and tuning") if traffic_src else
+                                  "no capture of this kernel source and tuning",
                 "what": (f"algorithmic gather bytes (four {args.dtype.upper()} texels per voxel update) through the "
                          "L1 load data path"),
                 "peak_source": (f"derived from unit counts: 128 B/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz "
@@ -554,9 +584,12 @@ def run_ours(args, dist: Dist) -> dict | None:
 
     # --- end to end through the public API with host buffers
     if not args.no_e2e:
-        pinned = torch.empty(data.shape, dtype=data.dtype, pin_memory=True)
+        # page-locked host buffers backed by aligned huge pages (hostmem): the copies run at the link rate
+        # without the stalls that base-page pinned buffers show on hosts whose memory has been churned
+        from paper_1401_7494_gb300 import hostmem
+        pinned = hostmem.pinned_empty(data.shape, data.dtype)
         pinned.copy_(data)
-        vol_host = torch.empty((w.L,) * 3, dtype=torch.float32, pin_memory=True)
+        vol_host = hostmem.pinned_empty((w.L,) * 3, torch.float32)
         for _ in range(max(1, args.warmup)):
             bp.reset(stream)
             bp.backproject_host_read(pinned, vol_host, 0, w.n_views, stream)
@@ -625,13 +658,14 @@ def run_ours(args, dist: Dist) -> dict | None:
                          "h2d_bytes_per_step": int(pinned.numel() * pinned.element_size()),
                          "d2h_bytes_per_step": int(vol_host.numel() * 4),
                          "steps": e_steps,
-                         "api": "rct_backproject_host_read (pinned host buffers; the volume read-back overlaps the last pass)",
-                         "ms_per_step": round(e_ms / e_steps, 3),
-                         "step_ms": {"min": round(per_step[0], 3), "median": round(statistics.median(per_step), 3),
-                                     "max": round(per_step[-1], 3), "in_order": [round(t, 2) for t in in_order]},
-                         "host_enqueue_ms": [round(t, 2) for t in enqueue],
-                         "plain_copy_gbs": {"before": copy_before, "after": copy_after},
-                         "graph_replay": {
+                         "api": "rct_backproject_host_read (page-locked huge-page host buffers from hostmem.pinned_empty; "
+                                "the volume read-back overlaps the last pass)",
+                         "ms_per_step": round(e_ms / e_steps, 3)}
+        e2e_detail = {"step_ms": {"min": round(per_step[0], 3), "median": round(statistics.median(per_step), 3),
+                                  "max": round(per_step[-1], 3), "in_order": [round(t, 2) for t in in_order]},
+                      "host_enqueue_ms": [round(t, 2) for t in enqueue],
+                      "plain_copy_gbs": {"before": copy_before, "after": copy_after},
+                      "graph_replay": {
                              "value": round(dist.sum(float(w.updates * e_steps)) / (g_ms / 1e3) / 1e9, 2),
                              "unit": UNIT, "ms_per_step": round(g_ms / e_steps, 3),
                              "api": "the same call captured once with rct_graph_begin/end, replayed with rct_graph_launch",
@@ -687,6 +721,8 @@ def run_ours(args, dist: Dist) -> dict | None:
         result["cpu_baseline"] = {"value": round(gups, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                                   "sample": sample,
                                   "single_thread": {"value": round(one, 4), "unit": UNIT, "sample": one_sample}}
+    if not args.no_e2e:
+        result["e2e_detail"] = e2e_detail          # last key: it stays in the tail of a truncated log
     return result
 
 
@@ -701,19 +737,25 @@ def run_reference(args, dist: Dist) -> dict | None:
     host = w.projections(device="cuda" if _cuda_ok() else "cpu").cpu().numpy()
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     rates = []
+    step_ms = []
     cores = oracle.max_threads()
     sample = ""
     for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
         gups, cores, sample = oracle_rate(w, host, per_step)
         if i >= args.warmup:
             rates.append(gups)
+            step_ms.append((time.perf_counter() - t) * 1e3)
     value = statistics.median(rates)
-    ms_per_step = w.updates / (value * 1e9) * 1e3
+    # A step is one bounded sample of the reconstruction (a slab of z-planes x all views, sized for
+    # about per_step seconds); ms_per_step is the wall time those steps took, and the time a whole
+    # reconstruction would take at the measured rate is given beside it.
     return {"metric": METRIC_BY_DTYPE[args.dtype], "value": round(value, 4), "unit": UNIT, "n_gpus": dist.world,
             "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 1), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": round(statistics.median(step_ms), 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": dict(workload_config(args.workload, w, args.dtype), per_step_sample=sample),
+            "config": dict(workload_config(args.workload, w, args.dtype), per_step_sample=sample,
+                           ms_per_whole_reconstruction=round(w.updates / (value * 1e9) * 1e3, 1)),
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

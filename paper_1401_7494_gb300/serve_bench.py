@@ -17,7 +17,7 @@ import time
 
 import numpy as np
 
-from . import serving, tuning
+from . import hostmem, serving, tuning
 
 PROTOCOL_VIEWS = {"short124": 124, "short248": 248, "short496": 496}
 L_CHOICES = (128, 256, 512, 1024)
@@ -37,7 +37,7 @@ def build_protocols(device, det_w=1248, det_h=960, seed=1405, raw=False):
         kinds = [(name, dict())] + ([(name + "/raw", dict(weighted=False, filtered=False))] if raw else [])
         for key, kw in kinds:
             proj = synth.make_projections(w.geom, w.phantom, device=device, **kw)
-            pinned = torch.empty(proj.shape, dtype=torch.float32, pin_memory=True)
+            pinned = hostmem.pinned_empty(proj.shape, torch.float32)   # huge-page backed: no copy stalls
             pinned.copy_(proj)
             host[key] = pinned
             del proj

@@ -1,0 +1,73 @@
+"""Host buffers for the host-input path (paper_1401_7494_gb300.hostmem), on the CPU with a stand-in for
+the CUDA runtime's registration calls."""
+import gc
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1401_7494_gb300 import hostmem
+
+
+class FakeCudart:
+    def __init__(self):
+        self.registered = {}
+        self.unregistered = []
+
+    def cudaHostRegister(self, ptr, size, flags):
+        self.registered[ptr] = size
+        return 0
+
+    def cudaHostUnregister(self, ptr):
+        self.unregistered.append(ptr)
+        return 0
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    f = FakeCudart()
+    monkeypatch.setattr(torch.cuda, "cudart", lambda: f)
+    return f
+
+
+@pytest.mark.parametrize("shape,dtype", [((3, 5, 7), torch.float32), ((1000,), torch.float16), ((2, 3), torch.bfloat16)])
+def test_buffer_is_aligned_registered_and_zero(fake, shape, dtype):
+    t = hostmem.pinned_empty(shape, dtype)
+    assert tuple(t.shape) == shape and t.dtype == dtype and t.is_contiguous()
+    hp = hostmem.huge_page_bytes()
+    assert t.data_ptr() % hp == 0
+    assert t.data_ptr() in fake.registered
+    assert fake.registered[t.data_ptr()] >= t.numel() * t.element_size()
+    assert torch.count_nonzero(t) == 0
+    t.fill_(3)
+    assert float(t.float().sum()) == 3 * t.numel()
+
+
+def test_large_buffers_take_whole_huge_pages(fake, monkeypatch):
+    monkeypatch.setattr(hostmem, "huge_page_bytes", lambda: 1 << 20)
+    monkeypatch.setattr(hostmem, "huge_pages_enabled", lambda: True)
+    t = hostmem.pinned_empty((300, 1024), torch.float32)          # 1.17 MiB: two 1 MiB pages
+    assert t.data_ptr() % (1 << 20) == 0 and fake.registered[t.data_ptr()] == 2 << 20
+    small = hostmem.pinned_empty((1000,), torch.float32)          # far below a quarter page: base pages
+    assert fake.registered[small.data_ptr()] == 4000
+
+
+def test_buffer_lives_while_any_view_does(fake):
+    t = hostmem.pinned_empty((4, 1024), torch.float32)
+    addr = t.data_ptr()
+    view = t[2:]
+    view.fill_(1.5)
+    del t
+    gc.collect()
+    assert addr not in fake.unregistered             # the view still uses the memory
+    assert float(view.sum()) == 1.5 * view.numel()
+    del view
+    gc.collect()
+    assert addr in fake.unregistered                 # released with the last tensor
+
+
+def test_numpy_interop(fake):
+    t = hostmem.pinned_empty((6, 8), torch.float32)
+    a = t.numpy()
+    a[:] = np.arange(48, dtype=np.float32).reshape(6, 8)
+    assert float(t[5, 7]) == 47.0
