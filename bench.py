@@ -505,13 +505,15 @@ def run_ours(args, dist: Dist) -> dict | None:
              rct.RCT_GATHER_PAIR: "pld"}.get(tun.get("gather"), "tex")
     probe = lambda mode, code=rct.RCT_PROJ_F32: round(
         probes.rct_probe_texture(mode, code, px_per_voxel, px_per_voxel, 4096) / 1e9, 1)
-    probes = {"tex_tld4": probe(0), "ldg4": probe(3), "quad": probe(4), "pair": probe(5)}
+    fetch_probes = {"tex_tld4": probe(0), "ldg4": probe(3), "quad": probe(4), "pair": probe(5)}
     texel = 4 if args.dtype == "f32" else 2
     # The gather needs four texels (16 B FP32, 8 B 16-bit) per update from the L1/texture path.  Its
     # ceiling is the L1 load data path: 128 B per clock per SM x SMs x the SM clock measured during the run.
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    l1_peak = 128.0 * sms * sm_mhz * 1e6 / 1e9                        # GB/s
+    l1_derived = 128.0 * sms * sm_mhz * 1e6 / 1e9                     # GB/s
+    # the same path measured in this run: coalesced 16-byte loads that hit L1, over every SM
+    l1_peak = probes.rct_probe_l1_bandwidth(4096) / 1e9
     gather_gbs = kernel_gups * 4 * texel                              # GB/s of algorithmic texel bytes
     vol_bytes = 4 * w.L ** 3
     img_bytes = texel * w.geom.det_w * w.geom.det_h
@@ -545,11 +547,13 @@ def run_ours(args, dist: Dist) -> dict | None:
                                   "no capture of this kernel source and tuning",
                 "what": (f"algorithmic gather bytes (four {args.dtype.upper()} texels per voxel update) through the "
                          "L1 load data path"),
-                "peak_source": (f"derived from unit counts: 128 B/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz "
-                                "(median SM clock sampled during the timed region)"),
+                "peak_source": "measured in this run: rct_probe_l1_bandwidth (coalesced 16-byte loads that hit L1)",
+                "peak_derived": {"value": round(l1_derived, 1), "frac": round(gather_gbs / l1_derived, 4),
+                                 "source": f"128 B/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz (median SM clock sampled "
+                                           "during the timed region)"},
                 "kernel": f"bp_kernel, {route} route", "kernel_gups": round(kernel_gups, 1),
                 "kernel_share_of_step": round(kernel_ms / ms_total, 4), "updates_per_launch": int(upd_per_launch),
-                "fetch_probes_gfetch_s": probes, "probe_lane_stride_px": round(px_per_voxel, 2),
+                "fetch_probes_gfetch_s": fetch_probes, "probe_lane_stride_px": round(px_per_voxel, 2),
                 "issue": {"achieved": round(kernel_gups, 1), "peak": round(issue_peak_gups, 1), "unit": "GUPS",
                           "frac": round(kernel_gups / issue_peak_gups, 4),
                           "peak_source": "derived: 4 warp-instr/clk/SM x 32 lanes x SMs x SM clock / 20 issue slots "
@@ -661,7 +665,9 @@ def run_ours(args, dist: Dist) -> dict | None:
                          "api": "rct_backproject_host_read (page-locked huge-page host buffers from hostmem.pinned_empty; "
                                 "the volume read-back overlaps the last pass)",
                          "ms_per_step": round(e_ms / e_steps, 3)}
-        e2e_detail = {"step_ms": {"min": round(per_step[0], 3), "median": round(statistics.median(per_step), 3),
+        e2e_detail = {"host_buffers_huge_page_fraction": {"projections": round(hostmem.huge_fraction(pinned), 3),
+                                                          "volume": round(hostmem.huge_fraction(vol_host), 3)},
+                      "step_ms": {"min": round(per_step[0], 3), "median": round(statistics.median(per_step), 3),
                                   "max": round(per_step[-1], 3), "in_order": [round(t, 2) for t in in_order]},
                       "host_enqueue_ms": [round(t, 2) for t in enqueue],
                       "plain_copy_gbs": {"before": copy_before, "after": copy_after},

@@ -155,11 +155,13 @@ RCT_API rct_ctx *rct_create(int L, int det_w, int det_h, int n_views);
  * whole-volume context restricted to those planes: the device volume, and the
  * buffers rct_read_volume / rct_write_volume / rct_backproject_host_read
  * exchange, hold z_count * L * L floats (plane z_first first, then z-major
- * with x fastest); projections and matrices are the whole scan's.  When
- * z_first is a multiple of the z-run (every z-run divides 16), each plane is
- * bit for bit the same plane of a whole-volume context with the same tuning.
- * NULL on failure: z_first < 0, z_count < 1 or z_first + z_count > L give
- * RCT_EINVAL; the other failures are rct_create's.
+ * with x fastest); projections and matrices are the whole scan's.  Slab
+ * boundaries lie on multiples of 16 planes (z_first, and z_first + z_count
+ * unless it equals L): every z-run length divides 16, so the threads' runs
+ * are the whole-volume context's runs and each plane is bit for bit the same
+ * plane of a whole-volume context with the same tuning.  NULL on failure:
+ * an empty or out-of-range slab, or an unaligned boundary, gives RCT_EINVAL;
+ * the other failures are rct_create's.
  */
 RCT_API rct_ctx *rct_create_slab(int L, int det_w, int det_h, int n_views, int z_first, int z_count);
 /* Writes the planes a context holds (0 and L for rct_create). */

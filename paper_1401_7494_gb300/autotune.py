@@ -22,7 +22,7 @@ from . import rct, tuning
 CANDIDATES = {
     # (gather route, z positions per run through the texture gather when mixed)
     "gather": [(rct.RCT_GATHER_TLD4, 0), (rct.RCT_GATHER_LDG, 0), (rct.RCT_GATHER_QUAD, 0),
-               (rct.RCT_GATHER_PAIR, 0), (rct.RCT_GATHER_MIX, 1), (rct.RCT_GATHER_MIX, 2),
+               (rct.RCT_GATHER_PAIR, 0), (rct.RCT_GATHER_DQUAD, 0), (rct.RCT_GATHER_MIX, 1), (rct.RCT_GATHER_MIX, 2),
                (rct.RCT_GATHER_MIX, 4), (rct.RCT_GATHER_MIX, 6)],
     "views_per_pass": [4, 8, 16, 24, 32],
     "zrun": [1, 2, 4, 8, 16],
@@ -31,8 +31,10 @@ CANDIDATES = {
 }
 
 
-def _valid(L: int, t: dict) -> bool:
+def _valid(L: int, t: dict, dtype: str = "f32") -> bool:
     bx, by = t["block_x"], t["block_y"]
+    if t.get("gather") == rct.RCT_GATHER_DQUAD and dtype != "f32":      # difference quads hold FP32 values
+        return False
     if t.get("gather") == rct.RCT_GATHER_MIX and not (1 <= t.get("tex_zrun", 0) < t["zrun"]):
         return False
     if t["zrun"] == 16 and t["xvec"] > 2:
@@ -132,7 +134,7 @@ def autotune(w, data, dtype: str = "f32", interp: str = "soft", n_views: int | N
                             t["gather"], t["tex_zrun"] = val
                         else:
                             t[p] = val
-                        if t == cur or not _valid(w.L, t):
+                        if t == cur or not _valid(w.L, t, dtype):
                             continue
                         g = measure(t)
                         if g > best * 1.01:

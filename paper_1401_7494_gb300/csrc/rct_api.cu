@@ -50,6 +50,7 @@ size_t dtype_size(int dt) { return dt == DT_F32 ? 4 : 2; }
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kReadSlabs = 8;   // z-slabs of the last pass when the read-back overlaps it
+constexpr int kSlabAlign = 16;  // slab contexts start and end on multiples of this many planes
 
 // One staging slot: a 2D CUDA array that holds one view for texture sampling.
 struct Slot {
@@ -436,11 +437,17 @@ LaunchConfig launch_config(const rct_ctx *c, int kind) {
 
 void init_params(const rct_ctx *c, BpParams *p) {
     std::memset(p, 0, sizeof *p);
-    p->vol = c->vol;
-    p->vol_z0 = c->z_first;
+    // The kernels address plane z at vol + z * L * L; a slab context's buffer starts at plane z_first, so
+    // the address it passes lies z_first planes before the buffer (integer arithmetic: only the slab's
+    // planes are ever touched, the launches cover whole z-runs inside the slab).
+    p->vol = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(c->vol) -
+                                       static_cast<uintptr_t>(c->z_first) * c->L * c->L * sizeof(float));
     p->z_base = c->z_first;
     p->z_count = c->z_count;
+#ifdef RCT_CHECK_BOUNDS
+    p->vol_z0 = c->z_first;
     p->vol_elems = static_cast<long long>(c->z_count) * c->L * c->L;
+#endif
     p->L = c->L;
     p->W = c->W;
     p->H = c->H;
@@ -664,6 +671,12 @@ rct_ctx *rct_create_slab(int L, int det_w, int det_h, int n_views, int z_first, 
     if (z_first < 0 || z_count <= 0 || z_count > L - z_first) {
         fail(RCT_EINVAL, "rct_create_slab: planes [%d, %lld) are not a non-empty range inside [0, %d)", z_first,
              (long long)z_first + z_count, L);
+        return nullptr;
+    }
+    // every z-run length divides kSlabAlign, so runs never cross a slab boundary
+    if (z_first % kSlabAlign != 0 || ((z_first + z_count) % kSlabAlign != 0 && z_first + z_count != L)) {
+        fail(RCT_EINVAL, "rct_create_slab: slab boundaries %d and %d must be multiples of %d planes (the end may "
+             "be L = %d)", z_first, z_first + z_count, kSlabAlign, L);
         return nullptr;
     }
     int dev = 0;

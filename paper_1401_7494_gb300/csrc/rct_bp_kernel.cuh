@@ -34,9 +34,7 @@
 //   * four predicated loads straight from the caller's linear image (no
 //     staging at all);
 //   * mixed: each z-run split between the texture gather and the quad load.
-// A view is skipped for a warp whose voxel runs all project off the detector,
-// and a warp whose voxel runs all project well inside it takes a path without
-// per-lane bounds tests, whose element address is two wide multiply-adds.
+// A view is skipped for a warp whose voxel runs all project off the detector.
 // Part 3: three lerps (two of them as one packed f32x2 pair) and
 // acc += val * r^2.
 #pragma once
@@ -100,12 +98,6 @@ struct ViewConsts {
     float2 gofs;     // t + gofs = gather corner (i0 + 1, j0 + 1)
     int cu, cv;
     int qcx, qcy;    // bits(t) - qc = padded quad index (i0 + 1, j0 + 1)
-    // Fast path (no bounds tests): the element of padded index (ix, jy) = (bits(t.x) - qcx,
-    // bits(t.y) - qcy) sits at base + (jy * EW + ix) * ES (EW elements of ES bytes per row), which is
-    // sbase + bits(t.y) * srow + bits(t.x) * ES with sbase = base - (qcy * EW + qcx) * ES and
-    // srow = EW * ES, all modulo 2^64; for the linear image the same holds for the cell corner (i0, j0).
-    unsigned long long sbase;
-    unsigned srow;
     cudaTextureObject_t tex;
     const void *img;
     const void *quad;
@@ -122,20 +114,6 @@ struct ViewConsts {
 //   ROUTE_PLD: every z position by two loads of staged vertical pairs.
 //   ROUTE_DQD: every z position by one load of a staged difference quad (FP32).
 enum Route : int { ROUTE_TEX = 0, ROUTE_LDG = 1, ROUTE_QLD = 2, ROUTE_MIX = 3, ROUTE_PLD = 4, ROUTE_DQD = 5 };
-
-// Routes with a path for warps whose every lane is known to fetch on the image.
-template <int ROUTE, bool TRUNC>
-constexpr bool has_fast_path() {
-    return !TRUNC && (ROUTE == ROUTE_LDG || ROUTE == ROUTE_QLD || ROUTE == ROUTE_PLD || ROUTE == ROUTE_DQD);
-}
-
-// Fast-path address (see ViewConsts::sbase): two wide multiply-adds of the floor's bit patterns.
-template <int ES>
-__device__ __forceinline__ const char *fast_addr(const ViewConsts &c, float2 t) {
-    return reinterpret_cast<const char *>(
-        c.sbase + static_cast<unsigned long long>(__float_as_uint(t.y)) * static_cast<unsigned long long>(c.srow) +
-        static_cast<unsigned long long>(__float_as_uint(t.x)) * static_cast<unsigned long long>(ES));
-}
 
 // Floor and fraction of q = uv * r (r = 1 / w): the packed add of 1.5 * 2^23 rounded toward -inf
 // gives t = kMagic + floor(q), whose low bits are floor(q) as an integer; f = q - floor(q), formed by one
@@ -176,49 +154,25 @@ __device__ __forceinline__ void accumulate_tex(const ViewConsts &c, float2 t, fl
 // Part 2 + 3 by one load of the staged quad element (see ViewParams).  A cell with no tap on the
 // image has no element: such a lane loads element 0, which every off-image lane of the warp
 // shares (one cached sector), and adds it with weight 0.
-// Element pointer of a staged route: CHECKED tests the padded index (off-image lanes go to element
-// 0 with weight 0); otherwise the caller guarantees every lane is on the image (fast path).
-template <int ES, int EXTRA, bool CHECKED>
-__device__ __forceinline__ const char *staged_elem(const ViewConsts &c, float2 t, int W, int H, int EW, float &w2) {
-    if constexpr (CHECKED) {
-        const int ix = __float_as_int(t.x) - c.qcx;                         // padded index (i0 + 1, j0 + 1)
-        const int jy = __float_as_int(t.y) - c.qcy;
-        const bool on = static_cast<unsigned>(ix) <= static_cast<unsigned>(W) &&
-                        static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
-        const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(EW) + static_cast<unsigned>(ix) : 0u;
-        w2 = on ? w2 : 0.0f;
-#ifdef RCT_CHECK_BOUNDS
-        if (!rct_in_bounds(static_cast<long long>(e) + EXTRA < c.qelems, c.viol)) return nullptr;
-#endif
-        return static_cast<const char *>(c.quad) + static_cast<size_t>(e) * ES;
-    } else {
-#ifdef RCT_CHECK_BOUNDS
-        {
-            const long long ix = __float_as_int(t.x) - c.qcx, jy = __float_as_int(t.y) - c.qcy;
-            const long long e = jy * EW + ix;
-            if (!rct_in_bounds(ix >= 0 && ix <= W && jy >= 0 && jy <= H && e >= 0 && e + EXTRA < c.qelems, c.viol))
-                return nullptr;
-        }
-#endif
-        return fast_addr<ES>(c, t);
-    }
-}
-
-template <int DT, bool CHECKED = true>
+template <int DT>
 __device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 t, float2 f, float w2, int W, int H,
                                                 float &acc) {
-    constexpr int ES = DT == DT_F32 ? 16 : 8;
-    const char *ep = staged_elem<ES, 0, CHECKED>(c, t, W, H, W + 1, w2);
+    const int ix = __float_as_int(t.x) - c.qcx;                             // padded index (i0 + 1, j0 + 1)
+    const int jy = __float_as_int(t.y) - c.qcy;
+    const bool on = static_cast<unsigned>(ix) <= static_cast<unsigned>(W) &&
+                    static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
+    const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 1) + static_cast<unsigned>(ix) : 0u;
+    w2 = on ? w2 : 0.0f;
 #ifdef RCT_CHECK_BOUNDS
-    if (!ep) return;
+    if (!rct_in_bounds(static_cast<long long>(e) < c.qelems, c.viol)) return;
 #endif
     float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
     if constexpr (DT == DT_F32) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(ep));
+        const float4 v = __ldg(static_cast<const float4 *>(c.quad) + e);
         ac = make_float2(v.x, v.y);
         bd = make_float2(v.z, v.w);
     } else {
-        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(ep));
+        const uint2 v = __ldg(static_cast<const uint2 *>(c.quad) + e);
         if constexpr (DT == DT_F16) {
             ac = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
             bd = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
@@ -234,21 +188,25 @@ __device__ __forceinline__ void accumulate_quad(const ViewConsts &c, float2 t, f
 
 // Part 2 + 3 by two loads of consecutive staged vertical pairs (see ViewParams): neighbouring
 // lanes share cache sectors, so less data moves from L2 than with quads.  Same off-image rule.
-template <int DT, bool CHECKED = true>
+template <int DT>
 __device__ __forceinline__ void accumulate_pair(const ViewConsts &c, float2 t, float2 f, float w2, int W, int H,
                                                 float &acc) {
-    constexpr int ES = DT == DT_F32 ? 8 : 4;
-    const char *ep = staged_elem<ES, 1, CHECKED>(c, t, W, H, W + 2, w2);
+    const int ix = __float_as_int(t.x) - c.qcx;                             // padded index (i0 + 1, j0 + 1)
+    const int jy = __float_as_int(t.y) - c.qcy;
+    const bool on = static_cast<unsigned>(ix) <= static_cast<unsigned>(W) &&
+                    static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
+    const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 2) + static_cast<unsigned>(ix) : 0u;
+    w2 = on ? w2 : 0.0f;
 #ifdef RCT_CHECK_BOUNDS
-    if (!ep) return;
+    if (!rct_in_bounds(static_cast<long long>(e) + 1 < c.qelems, c.viol)) return;
 #endif
     float2 ac, bd;                                                          // (I[j0][i0], I[j0+1][i0]), (I[j0][i0+1], I[j0+1][i0+1])
     if constexpr (DT == DT_F32) {
-        const float2 *pp = reinterpret_cast<const float2 *>(ep);
+        const float2 *pp = static_cast<const float2 *>(c.quad) + e;
         ac = __ldg(pp);
         bd = __ldg(pp + 1);
     } else {
-        const unsigned *pp = reinterpret_cast<const unsigned *>(ep);
+        const unsigned *pp = static_cast<const unsigned *>(c.quad) + e;
         const unsigned v0 = __ldg(pp), v1 = __ldg(pp + 1);
         if constexpr (DT == DT_F16) {
             ac = __half22float2(*reinterpret_cast<const __half2 *>(&v0));
@@ -263,39 +221,25 @@ __device__ __forceinline__ void accumulate_pair(const ViewConsts &c, float2 t, f
 }
 
 // Part 2 + 3 by one load of a staged difference quad (FP32; see ViewParams): both rows' lerps along x
-// in one packed FMA, with the roundings of the quad and pair routes (bitwise the same sums).
-template <bool CHECKED = true>
+// in one packed FMA, with the roundings the quad and pair routes perform (bitwise the same sums).
+// Same off-image rule as the quads.
 __device__ __forceinline__ void accumulate_dquad(const ViewConsts &c, float2 t, float2 f, float w2, int W, int H,
                                                  float &acc) {
-    const char *ep = staged_elem<16, 0, CHECKED>(c, t, W, H, W + 1, w2);
+    const int ix = __float_as_int(t.x) - c.qcx;                             // padded index (i0 + 1, j0 + 1)
+    const int jy = __float_as_int(t.y) - c.qcy;
+    const bool on = static_cast<unsigned>(ix) <= static_cast<unsigned>(W) &&
+                    static_cast<unsigned>(jy) <= static_cast<unsigned>(H);
+    const unsigned e = on ? static_cast<unsigned>(jy) * static_cast<unsigned>(W + 1) + static_cast<unsigned>(ix) : 0u;
+    w2 = on ? w2 : 0.0f;
 #ifdef RCT_CHECK_BOUNDS
-    if (!ep) return;
+    if (!rct_in_bounds(static_cast<long long>(e) < c.qelems, c.viol)) return;
 #endif
-    const float4 v = __ldg(reinterpret_cast<const float4 *>(ep));          // (a, c, b - a, d - c)
+    const float4 v = __ldg(static_cast<const float4 *>(c.quad) + e);      // (a, c, b - a, d - c)
     const float2 rows = __ffma2_rn(make_float2(f.x, f.x), make_float2(v.z, v.w), make_float2(v.x, v.y));
     acc = fmaf(fmaf(f.y, rows.y - rows.x, rows.x), w2, acc);
 }
 
-// Part 2 + 3 by four loads from the caller's linear image (no staging): predicated per tap, or, on
-// the fast path (every lane's cell wholly on the image), unconditional.
-template <int DT>
-__device__ __forceinline__ void accumulate_ldg_fast(const ViewConsts &c, float2 t, float2 f, float w2, int W, int H,
-                                                    float &acc) {
-    constexpr int ES = DT == DT_F32 ? 4 : 2;
-#ifdef RCT_CHECK_BOUNDS
-    {
-        const long long i0 = __float_as_int(t.x) - kMagicBits + c.cu, j0 = __float_as_int(t.y) - kMagicBits + c.cv;
-        if (!rct_in_bounds(i0 >= 0 && i0 + 1 < W && j0 >= 0 && j0 + 1 < H, c.viol)) return;
-    }
-#endif
-    const char *p0 = fast_addr<ES>(c, t);
-    const char *p1 = p0 + static_cast<size_t>(W) * ES;
-    const float a = load_px<DT>(p0, 0), b = load_px<DT>(p0, 1), cc = load_px<DT>(p1, 0), d = load_px<DT>(p1, 1);
-    const float t0 = fmaf(f.x, b - a, a);
-    const float t1 = fmaf(f.x, d - cc, cc);
-    acc = fmaf(fmaf(f.y, t1 - t0, t0), w2, acc);
-}
-
+// Part 2 + 3 by four predicated loads from the caller's linear image (no staging).
 template <int DT>
 __device__ __forceinline__ void accumulate_ldg(const ViewConsts &c, float2 t, float2 f, float w2, int W, int H, float &acc) {
     const int i0 = __float_as_int(t.x) - kMagicBits + c.cu;
@@ -362,60 +306,6 @@ __device__ __forceinline__ void block_frame(const ViewGeo *vg, float bX, float b
     out[2] = make_float4(fmaf(-cub, hw.z, h1.x), fmaf(-cvb, hw.z, h1.y), __int_as_float(sh.y + static_cast<int>(cvb)), 0.f);
 }
 
-// One view's updates of a thread's run: R z positions x XV x positions from the base coordinates
-// (buv, bw) of its first voxel.  CHECKED = false is the fast path: the caller has shown that every
-// lane's cell of every voxel lies on the staged image (or, for plain loads, wholly on the image).
-template <int G, int DT, int XV, int R, int ROUTE, bool TRUNC, bool CHECKED>
-__device__ __forceinline__ void run_view(const ViewConsts &c, float2 buv, float bw, float2 m_x, float mwx, int W, int H,
-                                         int tex_zrun, float (&acc)[R][XV]) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const float fr = static_cast<float>(r);
-        const float2 uvr = __ffma2_rn(make_float2(fr, fr), c.m_z, buv);
-        const float wr = fmaf(fr, c.w_z, bw);
-#pragma unroll
-        for (int j = 0; j < XV; ++j) {
-            const float fj = static_cast<float>(j);
-            const float2 uv = (j == 0) ? uvr : __ffma2_rn(make_float2(fj, fj), m_x, uvr);
-            const float w = (j == 0) ? wr : fmaf(fj, mwx, wr);
-            const float rw = rcp_approx(w);
-            const float w2 = rw * rw;
-            if constexpr (G == G_TEXLIN) {
-                // Texture-unit bilinear; the matrix already carries the +0.5 texel-centre shift.
-                const float2 q = __fmul2_rn(uv, make_float2(rw, rw));
-                acc[r][j] = fmaf(tex2D<float>(c.tex, q.x, q.y), w2, acc[r][j]);
-            } else {
-                float2 t, f;
-                floor_frac(uv, rw, t, f);
-                if constexpr (TRUNC) {
-                    // (int) of a negative coordinate with a fraction is floor + 1: the cell moves one
-                    // pixel right and its fraction becomes f - 1 (the listing then extrapolates).
-                    const float ax = (__float_as_int(t.x) <= c.qcx && f.x != 0.0f) ? 1.0f : 0.0f;
-                    const float ay = (__float_as_int(t.y) <= c.qcy && f.y != 0.0f) ? 1.0f : 0.0f;
-                    t = __fadd2_rn(t, make_float2(ax, ay));
-                    f = __fadd2_rn(f, make_float2(-ax, -ay));
-                }
-                if constexpr (ROUTE == ROUTE_TEX) {
-                    accumulate_tex<DT>(c, t, f, w2, acc[r][j]);
-                } else if constexpr (ROUTE == ROUTE_LDG) {
-                    if constexpr (CHECKED) accumulate_ldg<DT>(c, t, f, w2, W, H, acc[r][j]);
-                    else accumulate_ldg_fast<DT>(c, t, f, w2, W, H, acc[r][j]);
-                } else if constexpr (ROUTE == ROUTE_QLD) {
-                    accumulate_quad<DT, CHECKED>(c, t, f, w2, W, H, acc[r][j]);
-                } else if constexpr (ROUTE == ROUTE_PLD) {
-                    accumulate_pair<DT, CHECKED>(c, t, f, w2, W, H, acc[r][j]);
-                } else if constexpr (ROUTE == ROUTE_DQD) {
-                    accumulate_dquad<CHECKED>(c, t, f, w2, W, H, acc[r][j]);
-                } else if (r < tex_zrun) {
-                    accumulate_tex<DT>(c, t, f, w2, acc[r][j]);
-                } else {
-                    accumulate_quad<DT>(c, t, f, w2, W, H, acc[r][j]);
-                }
-            }
-        }
-    }
-}
-
 // FRAME: block frames (needs p.geo) instead of the global frame; the texture-filtered kernel
 // always takes the global frame (the texture unit needs absolute coordinates).
 // TRUNC: the cell index of Listing 1's (int) cast, which truncates toward zero, instead of floor
@@ -425,16 +315,6 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
     static_assert(!FRAME || G == G_SOFT, "block frames are for the software gathers");
     static_assert(!TRUNC || (G == G_SOFT && ROUTE == ROUTE_LDG && !FRAME), "truncation: global frame, plain loads");
     static_assert(ROUTE != ROUTE_DQD || DT == DT_F32, "difference quads hold FP32 values");
-    constexpr bool kFast = G == G_SOFT && has_fast_path<ROUTE, TRUNC>();
-    // fast-path geometry of the fetched buffer: elements per row and bytes per element
-    constexpr int kES = ROUTE == ROUTE_PLD ? (DT == DT_F32 ? 8 : 4)
-                      : (ROUTE == ROUTE_QLD || ROUTE == ROUTE_DQD) ? (DT == DT_F32 ? 16 : 8)
-                      : (DT == DT_F32 ? 4 : 2);
-    const int kEW = ROUTE == ROUTE_PLD ? p.W + 2 : (ROUTE == ROUTE_QLD || ROUTE == ROUTE_DQD) ? p.W + 1 : p.W;
-    // padded-index margin a run's corners must keep from the staged image's edge for the fast path (one
-    // more for plain loads, whose cell must lie wholly on the image); the extra pixel absorbs the
-    // difference between the corners' fused floor and the voxels' own
-    constexpr int kLo = ROUTE == ROUTE_LDG ? 2 : 1;
     const int L = p.L;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * XV;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -447,15 +327,14 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
     const float ly = static_cast<float>(threadIdx.y);
 
     const bool inside = x0 < L && y < L;
-    const int zlim = p.z_count > 0 ? p.z_base + p.z_count : L;   // first plane this launch must not touch
     const size_t plane = static_cast<size_t>(L) * L;
-    float *vb = p.vol + (inside ? static_cast<size_t>(z0 - p.vol_z0) * plane + static_cast<size_t>(y) * L + x0 : 0);
+    float *vb = p.vol + (inside ? static_cast<size_t>(z0) * plane + static_cast<size_t>(y) * L + x0 : 0);
     // The volume rows of the run are requested into L2 first (without holding registers), so the
     // DRAM latency overlaps the set-up below.
     if (inside && p.accumulate) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (z0 + r < zlim) asm volatile("prefetch.global.L2 [%0];" :: "l"(vb + r * plane));
+            if (z0 + r < L) asm volatile("prefetch.global.L2 [%0];" :: "l"(vb + r * plane));
     }
 
     // Block frames of the pass's views: lane k of the first warp evaluates view k once for the
@@ -473,7 +352,7 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
     float acc[R][XV];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        bool live = p.accumulate && (z0 + r < zlim);
+        bool live = p.accumulate && (z0 + r < L);
 #ifdef RCT_CHECK_BOUNDS
         {
             const long long at = static_cast<long long>(z0 + r - p.vol_z0) * L * L + static_cast<long long>(y) * L + x0;
@@ -535,16 +414,6 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
         c.gofs = make_float2(-(kMagic - static_cast<float>(c.cu + 1)), -(kMagic - static_cast<float>(c.cv + 1)));
         c.qcx = kMagicBits - c.cu - 1;
         c.qcy = kMagicBits - c.cv - 1;
-        if constexpr (kFast) {
-            // linear image: the cell corner (i0, j0) = (bits(t.x) - (qcx + 1), bits(t.y) - (qcy + 1))
-            const unsigned ox = static_cast<unsigned>(c.qcx) + (ROUTE == ROUTE_LDG ? 1u : 0u);
-            const unsigned oy = static_cast<unsigned>(c.qcy) + (ROUTE == ROUTE_LDG ? 1u : 0u);
-            const void *base = ROUTE == ROUTE_LDG ? v.img : v.quad;
-            c.srow = static_cast<unsigned>(kEW) * kES;
-            c.sbase = reinterpret_cast<unsigned long long>(base) -
-                      (static_cast<unsigned long long>(oy) * static_cast<unsigned>(kEW) + ox) * kES;
-        }
-        bool safe = kFast;
         if constexpr (G == G_SOFT) {
             // Clipping per run (the paper's clipping mask, Section "Implementation"): the
             // thread's voxels form a segment (XV = 1) or parallelogram in (x, z); its projection
@@ -566,22 +435,60 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
                     right = right && ci.x > p.W;
                     top = top && ci.y < (TRUNC ? -1 : 0);
                     bottom = bottom && ci.y > p.H;
-                    safe = safe && ci.x >= kLo && ci.x <= p.W - kLo && ci.y >= kLo && ci.y <= p.H - kLo;
                 }
             }
             if (__all_sync(0xffffffffu, left || right || top || bottom)) continue;
         }
-        if constexpr (kFast) {
-            if (__all_sync(0xffffffffu, safe)) {
-                run_view<G, DT, XV, R, ROUTE, TRUNC, false>(c, buv, bw, m_x, mw[0], p.W, p.H, tex_zrun, acc);
-                continue;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float fr = static_cast<float>(r);
+            const float2 uvr = __ffma2_rn(make_float2(fr, fr), c.m_z, buv);
+            const float wr = fmaf(fr, c.w_z, bw);
+#pragma unroll
+            for (int j = 0; j < XV; ++j) {
+                const float fj = static_cast<float>(j);
+                const float2 uv = (j == 0) ? uvr : __ffma2_rn(make_float2(fj, fj), m_x, uvr);
+                const float w = (j == 0) ? wr : fmaf(fj, mw[0], wr);
+                const float rw = rcp_approx(w);
+                const float w2 = rw * rw;
+                if constexpr (G == G_TEXLIN) {
+                    // Texture-unit bilinear; the matrix already carries the +0.5 texel-centre shift.
+                    const float2 q = __fmul2_rn(uv, make_float2(rw, rw));
+                    acc[r][j] = fmaf(tex2D<float>(c.tex, q.x, q.y), w2, acc[r][j]);
+                } else {
+                    float2 t, f;
+                    floor_frac(uv, rw, t, f);
+                    if constexpr (TRUNC) {
+                        // (int) of a negative coordinate with a fraction is floor + 1: the cell moves one
+                        // pixel right and its fraction becomes f - 1 (the listing then extrapolates).
+                        const float ax = (__float_as_int(t.x) <= c.qcx && f.x != 0.0f) ? 1.0f : 0.0f;
+                        const float ay = (__float_as_int(t.y) <= c.qcy && f.y != 0.0f) ? 1.0f : 0.0f;
+                        t = __fadd2_rn(t, make_float2(ax, ay));
+                        f = __fadd2_rn(f, make_float2(-ax, -ay));
+                    }
+                    if constexpr (ROUTE == ROUTE_TEX) {
+                        accumulate_tex<DT>(c, t, f, w2, acc[r][j]);
+                    } else if constexpr (ROUTE == ROUTE_LDG) {
+                        accumulate_ldg<DT>(c, t, f, w2, p.W, p.H, acc[r][j]);
+                    } else if constexpr (ROUTE == ROUTE_QLD) {
+                        accumulate_quad<DT>(c, t, f, w2, p.W, p.H, acc[r][j]);
+                    } else if constexpr (ROUTE == ROUTE_PLD) {
+                        accumulate_pair<DT>(c, t, f, w2, p.W, p.H, acc[r][j]);
+                    } else if constexpr (ROUTE == ROUTE_DQD) {
+                        accumulate_dquad(c, t, f, w2, p.W, p.H, acc[r][j]);
+                    } else if (r < tex_zrun) {
+                        accumulate_tex<DT>(c, t, f, w2, acc[r][j]);
+                    } else {
+                        accumulate_quad<DT>(c, t, f, w2, p.W, p.H, acc[r][j]);
+                    }
+                }
             }
         }
-        run_view<G, DT, XV, R, ROUTE, TRUNC, true>(c, buv, bw, m_x, mw[0], p.W, p.H, tex_zrun, acc);
     }
+
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        if (z0 + r >= zlim) break;
+        if (z0 + r >= L) break;
 #ifdef RCT_CHECK_BOUNDS
         {
             const long long at = static_cast<long long>(z0 + r - p.vol_z0) * L * L + static_cast<long long>(y) * L + x0;

@@ -63,8 +63,9 @@ struct __align__(16) ViewGeo {
 // [0, W] x [0, H]; a kernel tests that and sends every other lane to element 0.
 
 struct BpParams {
-    float *vol;      // planes [vol_z0, vol_z0 + planes held) of the L^3 volume, z-major, x fastest
-    int vol_z0;      // z plane of vol[0] (0 for a whole-volume context; z_first of a slab context)
+    float *vol;      // L^3, z-major, x fastest: the address of plane 0 (for a slab context, which holds
+                     // planes [z_first, z_first + z_count) only, an address z_first planes before its buffer;
+                     // no plane outside the slab is touched)
     int L, W, H;
     int K;           // views in this pass, 1..KMAX
     float cen;       // (L - 1) / 2
@@ -75,10 +76,12 @@ struct BpParams {
     const ViewGeo *geo;  // G_SOFT: the context's per-view geometry for block frames (null: global frame)
     int first_view;      // view index of view[0] in geo
     int z_base;          // first z plane of this launch (0: the whole volume)
-    int z_count;         // z planes from z_base (0: up to L); the launch writes no plane at or past
-                         // z_base + z_count
+    int z_count;         // z planes from z_base (0: all L); a multiple of the z-run unless it ends at L
     long long qelems;    // elements of one staged quad / pair image (bounds-checking build only)
-    long long vol_elems; // floats held at vol (bounds-checking build only)
+#ifdef RCT_CHECK_BOUNDS
+    int vol_z0;          // bounds-checking build: first plane the volume buffer holds
+    long long vol_elems; // bounds-checking build: floats the volume buffer holds
+#endif
     unsigned long long *viol;  // bounds-checking build: violation counter on the device (null: not counted)
     ViewParams view[KMAX];
 };

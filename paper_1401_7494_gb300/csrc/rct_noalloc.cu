@@ -119,7 +119,9 @@ extern "C" rct_status rct_backproject_f16_noalloc(int L, int det_w, int det_h, c
     lc.by = 8;
     BpParams p{};
     p.vol = d_volume;
+#ifdef RCT_CHECK_BOUNDS
     p.vol_elems = static_cast<long long>(L) * L * L;
+#endif
     p.L = L;
     p.W = det_w;
     p.H = det_h;

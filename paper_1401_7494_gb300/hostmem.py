@@ -13,8 +13,10 @@ pages that are aligned to the huge-page size never stalled: 80 copies of
 buffers, no step slower than the median.
 
 ``pinned_empty`` allocates such a buffer: an anonymous mapping aligned to
-the huge-page size, advised for transparent huge pages, touched once, and
-registered with ``cudaHostRegister``.  The returned tensor owns the buffer:
+the huge-page size, advised for transparent huge pages, touched once,
+collapsed into huge pages where the first touch did not get them (a host
+with fragmented memory), and registered with ``cudaHostRegister``;
+``huge_fraction`` reports how much of a buffer huge pages back.  The returned tensor owns the buffer:
 it is unregistered and unmapped when the tensor and every view of it are
 gone.  Where transparent huge pages are switched off the buffer is still
 aligned, locked and registered, in base pages.
@@ -28,6 +30,7 @@ from pathlib import Path
 _PROT_RW = 0x1 | 0x2
 _MAP_PRIVATE_ANON = 0x02 | 0x20
 _MADV_HUGEPAGE = 14
+_MADV_COLLAPSE = 25       # Linux 6.1+: make the range huge pages now (compacting memory if it must)
 _THP = Path("/sys/kernel/mm/transparent_hugepage")
 
 _libc = None
@@ -96,8 +99,34 @@ def pinned_empty(shape, dtype):
     mapping = _Mapping.from_address(start)
     t = torch.frombuffer(mapping, dtype=torch.uint8)
     t.zero_()                                     # touch every page before it is locked
+    if huge:
+        libc.madvise(start, size, _MADV_COLLAPSE)  # best effort: fails harmlessly where unsupported
     err = cudart.cudaHostRegister(start, size, 0)
     if int(err) != 0:
         raise RuntimeError(f"cudaHostRegister of {size} bytes failed: {err}")
     mapping.registered = True
     return t[:nbytes].view(dtype).view(*[int(s) for s in shape])
+
+
+def huge_fraction(t) -> float:
+    """Fraction of the memory mapping that holds tensor ``t`` which transparent huge pages back (from
+    /proc/self/smaps; 0.0 where the mapping is not found)."""
+    addr = t.data_ptr()
+    try:
+        lines = Path("/proc/self/smaps").read_text().splitlines()
+    except OSError:
+        return 0.0
+    inside = False
+    size = huge = 0
+    for line in lines:
+        head = line.split()[0] if line.split() else ""
+        if "-" in head and ":" not in head:
+            lo, hi = (int(x, 16) for x in head.split("-"))
+            inside = lo <= addr < hi
+            continue
+        if inside and line.startswith("Size:"):
+            size = int(line.split()[1])
+        elif inside and line.startswith("AnonHugePages:"):
+            huge = int(line.split()[1])
+            break
+    return huge / size if size else 0.0

@@ -33,7 +33,8 @@ def main():
     cases["far"] = far
     G = rct
     tunings = []
-    for gather in (G.RCT_GATHER_TLD4, G.RCT_GATHER_LDG, G.RCT_GATHER_QUAD, G.RCT_GATHER_PAIR, G.RCT_GATHER_MIX):
+    for gather in (G.RCT_GATHER_TLD4, G.RCT_GATHER_LDG, G.RCT_GATHER_QUAD, G.RCT_GATHER_PAIR, G.RCT_GATHER_MIX,
+                   G.RCT_GATHER_DQUAD):
         for zrun, xvec in ((1, 1), (2, 2), (4, 4), (8, 1), (16, 2)):
             tunings.append(dict(gather=gather, zrun=zrun, xvec=xvec, tex_zrun=1, views_per_pass=7,
                                 block_x=16, block_y=8))
@@ -73,6 +74,22 @@ def main():
                     bp.backproject(data, 0, w.n_views, stream)
                     violations += rct.rct_debug_bound_violations(bp.ctx)
                     runs += 1
+    # Slab contexts: every plane index stays inside the slab's own buffer, through the device and host paths.
+    w = cases["L40"]
+    proj = w.projections(device=dev)
+    for z0, zc in ((0, 16), (16, 16), (32, 8), (16, 24)):
+        for gather, zrun in ((G.RCT_GATHER_PAIR, 16), (G.RCT_GATHER_DQUAD, 8), (G.RCT_GATHER_LDG, 4)):
+            with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views, z_range=(z0, zc)) as bp:
+                bp.set_geometry(w.geom.matrices, w.origin, w.spacing)
+                bp.set_tuning(gather=gather, zrun=zrun, xvec=1, views_per_pass=7)
+                out = torch.empty((zc, w.L, w.L), dtype=torch.float32, device=dev)
+                if zrun == 4:
+                    bp.backproject_host_read(proj.cpu().pin_memory(), out, 0, w.n_views, stream)
+                else:
+                    bp.backproject(proj, 0, w.n_views, stream)
+                    bp.read_volume(out, stream)
+                violations += rct.rct_debug_bound_violations(bp.ctx)
+                runs += 1
     # Control: with the bounds checks' staged-image limit lowered to a tenth of the image, in-bounds pair loads
     # past it are counted (and skipped); restored, the count stops growing.
     w = cases["L40"]

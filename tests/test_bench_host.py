@@ -54,14 +54,29 @@ def test_live_warp_fraction_matches_exhaustive_count():
         assert abs(est - exact) < 0.03, (bx, by, xv, R, est, exact)   # about 3 sampling standard deviations
 
 
-def test_traffic_table_keys():
-    for key, val in bench.TRAFFIC.items():
-        dtype, tun = key.split(" ", 1)
-        assert dtype in ("f32", "f16", "bf16")
-        t = json.loads(tun)
-        assert json.dumps(t, sort_keys=True) == tun          # looked up with sort_keys=True
-        assert set(t) == {"block_x", "block_y", "gather", "tex_zrun", "views_per_pass", "xvec", "zrun"}
-        assert 1e9 < val < 2e9                                # one accumulating pass at 512^3: ~1.1-1.3 GB
+def test_traffic_records(tmp_path, monkeypatch):
+    """Traffic per launch comes from a record in a profile summary, and counts only for the same storage
+    type, tuning and kernel source."""
+    for rec in bench.traffic_records():                     # every committed record is well formed
+        assert rec["dtype"] in ("f32", "f16", "bf16")
+        assert set(rec["tuning"]) == {"block_x", "block_y", "gather", "tex_zrun", "views_per_pass", "xvec", "zrun"}
+        assert 1e9 < rec["bytes"] < 2e9                       # one accumulating pass at 512^3: ~1.1-1.3 GB
+        assert len(rec["kernel_source"]) == 16
+    tun = {"block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0, "views_per_pass": 24, "xvec": 1, "zrun": 8}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rec = {"dtype": "f32", "tuning": tun, "kernel_source": bench.kernel_source_hash(), "bytes": 1269302272}
+    (prof / "x.md").write_text("# summary\n\ntraffic-record: " + json.dumps(rec) + "\n")
+    real_root = bench.ROOT
+    monkeypatch.setattr(bench, "ROOT", tmp_path)
+    for rel in bench.KERNEL_SOURCES:                        # the same kernel sources under the fake root
+        (tmp_path / rel).parent.mkdir(parents=True, exist_ok=True)
+        (tmp_path / rel).write_bytes((real_root / rel).read_bytes())
+    assert bench.recorded_traffic("f32", tun) == (1269302272, "x.md")
+    assert bench.recorded_traffic("f16", tun) == (None, None)
+    assert bench.recorded_traffic("f32", dict(tun, zrun=16)) == (None, None)
+    (tmp_path / bench.KERNEL_SOURCES[0]).write_text("// changed kernel\n")
+    assert bench.recorded_traffic("f32", tun) == (None, None)
 
 
 def _json_lines(text):

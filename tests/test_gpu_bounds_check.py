@@ -1,5 +1,5 @@
 """Bounds-checking build of the library (the stand-in for a memory sanitizer): every computed index of a
-staged image, of a plain-load tap and of the volume stays inside its buffer over all routes, z-runs,
+staged image, of a plain-load tap and of the volume stays inside its buffer over all routes, z-runs, slab contexts,
 x-vectors, frames, index rules, 16-bit storage, host input with overlapped read-back, a volume of one
 voxel and a volume entirely off the detector.  Needs a GPU; builds the checking variant on first use."""
 import json

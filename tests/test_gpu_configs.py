@@ -1,4 +1,4 @@
-"""Parity at the measured configurations: 496 views of 1248x960, L = 128 (every voxel) and
+"""Parity at the measured configurations: 496 views of 1248x960, L = 128 and 512 (every voxel) and
 L = 512 / 1024 (sampled voxels and whole planes), in the launch configuration the benchmark uses."""
 import numpy as np
 import pytest
@@ -26,6 +26,18 @@ def _sample_indices(L, seed, n_random=1 << 15, planes=(0,)):
     # the last row of the last plane: ragged x/y tails of the grid
     idx.append(np.arange(L, dtype=np.int64) + (L - 1) * L * L + (L - 1) * L)
     return np.unique(np.concatenate(idx))
+
+
+def test_full_parity_L512_496_views(cuda_device):
+    """The benchmark's workload and launch configuration, every one of the 512^3 voxels against the FP64
+    oracle (about 45 s of oracle work on 16 host cores)."""
+    w = synth.workloads.named("fp32_L512")
+    proj = w.projections(device=cuda_device)
+    host = proj.cpu().numpy()
+    got = gpu_backproject(w, proj, tuning=tuning_mod.lookup(w.L, "f32", "soft"))
+    del proj
+    ref = oracle_volume(w, host)
+    assert_parity(got, ref, "L=512 x 496 full volume")
 
 
 def test_full_parity_L128_496_views(cuda_device):
@@ -58,7 +70,9 @@ def test_sampled_parity_large(cuda_device, name, dtype, frame):
         bp.read_volume(vol, stream)
         torch.cuda.synchronize()
     del data
-    idx = _sample_indices(w.L, seed=w.seed, planes=(w.L // 2,))
+    # L = 1024: 2^20 random voxels and two whole planes; smaller volumes: 2^15 and one plane
+    idx = (_sample_indices(w.L, seed=w.seed, n_random=1 << 20, planes=(w.L // 4, (3 * w.L) // 4))
+           if w.L >= 1024 else _sample_indices(w.L, seed=w.seed, planes=(w.L // 2,)))
     got = vol.view(-1)[torch.from_numpy(idx).to(cuda_device)].cpu().numpy()
     del vol
     ref = _sampled_reference(w, oracle_inputs(host, dtype), idx)

@@ -57,10 +57,14 @@ def test_aligned_slabs_reproduce_the_whole_volume_bitwise(case, ti, parts):
     assert_parity(got, ref, f"{parts} slabs, tuning {TUNES[ti]}")
 
 
-def test_unaligned_slab_matches_the_oracle(case):
-    w, proj, ref = case
-    got = _slab_volume(w, proj, 5, 13, TUNES[0])
-    assert_parity(got, ref[5:18], "slab [5, 18)")
+def test_slab_boundaries_must_be_aligned(cuda_device):
+    """A z-run never crosses a slab boundary: boundaries lie on multiples of 16 planes (the end may be L)."""
+    for z0, zc in [(5, 13), (0, 20), (8, 8), (16, 20)]:
+        with pytest.raises(rct.RctError) as e:
+            rct.rct_create_slab(44, 64, 48, 4, z0, zc)
+        assert e.value.status == rct.RCT_EINVAL and "multiples" in rct.rct_last_error()
+    for z0, zc in [(0, 16), (16, 28), (32, 12), (0, 44)]:
+        rct.rct_destroy(rct.rct_create_slab(44, 64, 48, 4, z0, zc))
 
 
 @pytest.mark.parametrize("z_first,z_count", [(0, 16), (16, 28), (32, 12)])
@@ -83,11 +87,11 @@ def test_slab_range_errors(cuda_device):
 
 def test_slab_buffers_are_checked_against_the_slab(case):
     w, proj, _ = case
-    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views, z_range=(16, 12)) as bp:
-        small = torch.empty((11, w.L, w.L), dtype=torch.float32, device=proj.device)
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views, z_range=(16, 16)) as bp:
+        small = torch.empty((15, w.L, w.L), dtype=torch.float32, device=proj.device)
         with pytest.raises(ValueError):
             bp.read_volume(small)
-        ok = torch.empty((12, w.L, w.L), dtype=torch.float32, device=proj.device)
+        ok = torch.empty((16, w.L, w.L), dtype=torch.float32, device=proj.device)
         bp.read_volume(ok)
         torch.cuda.synchronize()
         assert float(ok.abs().max()) == 0.0          # a fresh context reads back zeros
