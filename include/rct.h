@@ -134,6 +134,12 @@ typedef struct rct_tuning {
     int block_y;         /* threads per block along y; block_x * block_y <= 512 */
     int gather;          /* rct_gather */
     int tex_zrun;        /* RCT_GATHER_MIX: z positions per run fetched by tld4, 1..zrun-1 */
+    int view_split;      /* 1, 2, 4 or 8: deal each pass's views out to this many groups of blocks, each adding
+                            into its own partial volume (the context holds view_split - 1 more volumes);
+                            the partials are added into the volume after each call's last pass.  More blocks
+                            per pass for small volumes; the per-voxel sum is regrouped (within the FP32
+                            parity bar of the plain order, deterministic).  Software gathers, global frame
+                            and floor rule only (RCT_ENOTSUP at the first backprojection call otherwise). */
 } rct_tuning;
 
 #define RCT_MAX_VIEWS_PER_PASS 32

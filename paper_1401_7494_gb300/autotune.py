@@ -28,6 +28,7 @@ CANDIDATES = {
     "zrun": [1, 2, 4, 8, 16],
     "xvec": [1, 2, 4],
     "block": [(32, 4), (32, 8), (32, 16), (64, 2), (64, 4), (16, 8), (16, 16), (8, 16), (128, 2)],
+    "view_split": [1, 2, 4, 8],
 }
 
 
@@ -38,6 +39,8 @@ def _valid(L: int, t: dict, dtype: str = "f32") -> bool:
     if t.get("gather") == rct.RCT_GATHER_MIX and not (1 <= t.get("tex_zrun", 0) < t["zrun"]):
         return False
     if t["zrun"] == 16 and t["xvec"] > 2:
+        return False
+    if t.get("view_split", 1) > 1 and t.get("view_split", 1) > t["views_per_pass"]:
         return False
     return L % t["xvec"] == 0 and bx * by <= 512 and (bx * by) % 32 == 0
 
@@ -96,6 +99,7 @@ def autotune(w, data, dtype: str = "f32", interp: str = "soft", n_views: int | N
         if cand not in starts:
             starts.append(dict(cand))
     for st in starts:
+        st.setdefault("view_split", 1)
         if w.L % st["xvec"]:
             st["xvec"] = 1
     trials = []
@@ -117,9 +121,10 @@ def autotune(w, data, dtype: str = "f32", interp: str = "soft", n_views: int | N
             log(f"  {t} -> {g:.1f} GUPS")
             return g
 
-        params = ["gather", "views_per_pass", "zrun", "xvec", "block"]
+        params = ["gather", "views_per_pass", "zrun", "xvec", "block", "view_split"]
         if interp == "tex":
             params.remove("gather")
+            params.remove("view_split")
         best_all, cur_all = -1.0, None
         for cur in starts:
             best = measure(cur)

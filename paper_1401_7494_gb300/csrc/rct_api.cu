@@ -132,6 +132,10 @@ struct rct_ctx {
     void *quad_buf = nullptr;
     size_t quad_alloc = 0;
 
+    // view split: view_split - 1 partial volumes of the context's planes
+    float *part = nullptr;
+    size_t part_alloc = 0;              // floats
+
     // host-input path: linear device staging (LDG) and the copy stream
     void *lin_stage = nullptr;
     size_t lin_stage_bytes = 0;
@@ -228,18 +232,24 @@ size_t layout_bytes(const rct_ctx *c) {
     return load_layout(c) == 2 ? pair_bytes(c->W, c->H, c->dtype) : quad_bytes(c->W, c->H, c->dtype);
 }
 
-cudaError_t launch_stage_layout(const rct_ctx *c, const void *src, void *dst, cudaStream_t s) {
+// Stages n consecutive views (src: n linear images back to back) into n consecutive staging slots from
+// dst, in one launch.
+cudaError_t launch_stage_layout(const rct_ctx *c, const void *src, void *dst, int n, cudaStream_t s) {
     switch (load_layout(c)) {
-        case 2: return launch_stage_pairs(src, dst, c->W, c->H, c->dtype, s);
-        case 3: return launch_stage_dquads(static_cast<const float *>(src), dst, c->W, c->H, s);
-        default: return launch_stage_quads(src, dst, c->W, c->H, c->dtype, s);
+        case 2: return launch_stage_pairs(src, dst, c->W, c->H, c->dtype, n, s);
+        case 3: return launch_stage_dquads(static_cast<const float *>(src), dst, c->W, c->H, n, s);
+        default: return launch_stage_quads(src, dst, c->W, c->H, c->dtype, n, s);
     }
 }
 
-// The difference-quad layout holds FP32 values only.
+// The difference-quad layout holds FP32 values only; the view split runs the software gathers in the
+// global frame with the floor rule.
 rct_status check_route(const rct_ctx *c) {
     if (gather_of(c) == RCT_GATHER_DQUAD && (c->dtype != DT_F32 || kernel_kind(c) != G_SOFT))
         return fail(RCT_ENOTSUP, "the difference-quad gather needs FP32 projections and software interpolation");
+    if (c->tune.view_split > 1 &&
+        (kernel_kind(c) != G_SOFT || c->frame != RCT_FRAME_GLOBAL || c->index_rule != RCT_INDEX_FLOOR))
+        return fail(RCT_ENOTSUP, "the view split needs software interpolation, the global frame and the floor rule");
     return RCT_OK;
 }
 
@@ -263,6 +273,7 @@ rct_tuning default_tuning(int L) {
     t.block_x = 32;
     t.block_y = 8;
     t.gather = RCT_GATHER_AUTO;
+    t.view_split = 1;
     (void)L;
     return t;
 }
@@ -407,6 +418,36 @@ void *quad_slot(const rct_ctx *c, int slot) {
     return static_cast<char *>(c->quad_buf) + (size_t)slot * layout_bytes(c);
 }
 
+size_t plane_floats(const rct_ctx *c) { return (size_t)c->L * c->L; }
+
+rct_status ensure_parts(rct_ctx *c) {
+    const int S = c->tune.view_split;
+    if (S <= 1) return RCT_OK;
+    const size_t need = (size_t)(S - 1) * c->z_count * plane_floats(c);
+    if (c->part_alloc >= need) return RCT_OK;
+    if (c->part) {
+        quiesce(c);
+        bump(c);
+        cudaFree(c->part);
+    }
+    c->part = nullptr;
+    c->part_alloc = 0;
+    cudaError_t e = cudaMalloc(&c->part, need * sizeof(float));
+    if (e != cudaSuccess) return fail(RCT_ENOMEM, "partial volumes of the view split: %zu bytes", need * sizeof(float));
+    c->part_alloc = need;
+    return RCT_OK;
+}
+
+// Adds the view split's partial volumes into planes [z, z + nz) of the volume (after a call's last pass).
+rct_status add_partials(rct_ctx *c, int z, int nz, cudaStream_t s) {
+    const int S = c->tune.view_split;
+    if (S <= 1 || nz <= 0) return RCT_OK;
+    const size_t at = (size_t)(z - c->z_first) * plane_floats(c);
+    cudaError_t e = launch_add_partials(c->vol + at, c->part + at, (size_t)nz * plane_floats(c),
+                                        (size_t)c->z_count * plane_floats(c), S - 1, s);
+    return e == cudaSuccess ? RCT_OK : cuda_fail(e, "adding the partial volumes");
+}
+
 rct_status ensure_widen(rct_ctx *c, size_t elems) {
     if (c->widen_elems >= elems) return RCT_OK;
     if (c->widen_buf) {
@@ -432,6 +473,7 @@ LaunchConfig launch_config(const rct_ctx *c, int kind) {
     lc.by = c->tune.block_y;
     lc.frame = (kind == G_SOFT && c->frame == RCT_FRAME_BLOCK) ? 1 : 0;
     lc.trunc = (kind == G_SOFT && c->index_rule == RCT_INDEX_TRUNC) ? 1 : 0;
+    lc.split = c->tune.view_split;
     return lc;
 }
 
@@ -448,6 +490,11 @@ void init_params(const rct_ctx *c, BpParams *p) {
     p->vol_z0 = c->z_first;
     p->vol_elems = static_cast<long long>(c->z_count) * c->L * c->L;
 #endif
+    if (c->tune.view_split > 1 && c->part) {       // the partial volumes, addressed like vol
+        p->part = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(c->part) -
+                                            static_cast<uintptr_t>(c->z_first) * c->L * c->L * sizeof(float));
+        p->part_stride = static_cast<long long>(c->z_count) * c->L * c->L;
+    }
     p->L = c->L;
     p->W = c->W;
     p->H = c->H;
@@ -742,6 +789,7 @@ void rct_destroy(rct_ctx *c) {
     if (c->vol) cudaFree(c->vol);
     if (c->lin_stage) cudaFree(c->lin_stage);
     if (c->quad_buf) cudaFree(c->quad_buf);
+    if (c->part) cudaFree(c->part);
     if (c->geo_dev) cudaFree(c->geo_dev);
     for (cudaEvent_t e : c->ev_slab) cudaEventDestroy(e);
     c->ev_slab.clear();
@@ -996,6 +1044,9 @@ rct_status rct_set_tuning(rct_ctx *c, const rct_tuning *t) {
         return fail(RCT_EINVAL, "block %dx%d: need a multiple of 32 threads, at most 512", n.block_x, n.block_y);
     if (n.gather < RCT_GATHER_AUTO || n.gather > RCT_GATHER_DQUAD) return fail(RCT_EINVAL, "unknown gather %d", n.gather);
     if (n.tex_zrun < 0 || n.tex_zrun > 16) return fail(RCT_EINVAL, "tex_zrun %d outside 0..16", n.tex_zrun);
+    if (t->view_split) n.view_split = t->view_split;
+    if (n.view_split != 1 && n.view_split != 2 && n.view_split != 4 && n.view_split != 8)
+        return fail(RCT_EINVAL, "view_split %d not in {1,2,4,8}", n.view_split);
     c->tune = n;
     return RCT_OK;
 }
@@ -1039,6 +1090,7 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
     if (staged && (st = ensure_copy_machinery(c))) return st;
     if ((st = ensure_slots(c, 2 * K))) return st;
     if ((st = ensure_quads(c, 2 * K))) return st;
+    if ((st = ensure_parts(c))) return st;
     if (kind == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
     const LaunchConfig lc = launch_config(c, kind);
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
@@ -1060,6 +1112,7 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
         p.K = kb;
         p.first_view = first_view + b;
         p.accumulate = c->vol_zero_pending ? 0 : 1;
+        p.accumulate_part = b > 0 ? 1 : 0;       // the call's first pass writes the partial volumes
         if (staged) RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[g], 0), "cudaStreamWaitEvent");
         for (int k = 0; k < kb; ++k) {
             ViewParams &vp = p.view[k];
@@ -1071,11 +1124,12 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
                 if ((st = stage_view(c, slot, src, false, c->copy_stream))) return st;
                 vp.tex = slot.tex;
             }
-            if (quad) {
-                vp.quad = quad_slot(c, g * K + k);
-                cudaError_t e = launch_stage_layout(c, src, const_cast<void *>(vp.quad), c->copy_stream);
-                if (e != cudaSuccess) return cuda_fail(e, "quad/pair staging kernel");
-            }
+            if (quad) vp.quad = quad_slot(c, g * K + k);
+        }
+        if (quad) {                  // the batch's views into its consecutive slots, one launch
+            cudaError_t e = launch_stage_layout(c, base + (size_t)b * view_bytes, quad_slot(c, g * K), kb,
+                                                c->copy_stream);
+            if (e != cudaSuccess) return cuda_fail(e, "quad/pair staging kernel");
         }
         if (staged) {
             RCT_CUDA(cudaEventRecord(c->ev_filled[g], c->copy_stream), "cudaEventRecord");
@@ -1086,6 +1140,7 @@ rct_status rct_backproject(rct_ctx *c, const void *d_proj, int first_view, int n
         c->vol_zero_pending = false;
         if (staged) RCT_CUDA(cudaEventRecord(c->ev_free[g], s), "cudaEventRecord");
     }
+    if ((st = add_partials(c, c->z_first, c->z_count, s))) return st;
     RCT_CUDA(mark_done(c, stream), "cudaEventRecord");
     return RCT_OK;
 }
@@ -1104,6 +1159,7 @@ rct_status backproject_host_impl(rct_ctx *c, const void *h_proj, int first_view,
     const size_t view_bytes = (size_t)c->W * c->H * dtype_size(c->dtype);
     if ((st = check_route(c))) return st;
     if ((st = ensure_host_staging(c))) return st;
+    if ((st = ensure_parts(c))) return st;
     const bool tex = uses_tex(c);
     const bool quad = uses_quad(c);
     const bool linear = host_needs_linear(c);
@@ -1126,25 +1182,30 @@ rct_status backproject_host_impl(rct_ctx *c, const void *h_proj, int first_view,
         p.K = kb;
         p.first_view = first_view + b;
         p.accumulate = c->vol_zero_pending ? 0 : 1;
+        p.accumulate_part = b > 0 ? 1 : 0;
+        // the batch's views sit back to back in host memory and go to consecutive linear slots: one copy
+        char *lin0 = linear ? static_cast<char *>(c->lin_stage) + (size_t)(g * K) * view_bytes : nullptr;
+        if (linear)
+            RCT_CUDA(cudaMemcpyAsync(lin0, base + (size_t)b * view_bytes, (size_t)kb * view_bytes,
+                                     cudaMemcpyHostToDevice, c->copy_stream), "cudaMemcpyAsync");
         for (int k = 0; k < kb; ++k) {
             const void *src = base + (size_t)(b + k) * view_bytes;
             ViewParams &vp = p.view[k];
             make_view(c, first_view + b + k, kind, &vp);
             Slot *slot = tex ? &c->slots[g * K + k] : nullptr;
             if (linear) {
-                char *lin = static_cast<char *>(c->lin_stage) + (size_t)(g * K + k) * view_bytes;
-                RCT_CUDA(cudaMemcpyAsync(lin, src, view_bytes, cudaMemcpyHostToDevice, c->copy_stream), "cudaMemcpyAsync");
+                char *lin = lin0 + (size_t)k * view_bytes;
                 if (slot && (st = stage_view(c, *slot, lin, false, c->copy_stream))) return st;
-                if (quad) {
-                    vp.quad = quad_slot(c, g * K + k);
-                    cudaError_t e = launch_stage_layout(c, lin, const_cast<void *>(vp.quad), c->copy_stream);
-                    if (e != cudaSuccess) return cuda_fail(e, "quad/pair staging kernel");
-                }
+                if (quad) vp.quad = quad_slot(c, g * K + k);
                 vp.img = lin;
             } else if (slot) {
                 if ((st = stage_view(c, *slot, src, true, c->copy_stream))) return st;
             }
             if (slot) vp.tex = slot->tex;
+        }
+        if (linear && quad) {        // the batch's views into its consecutive slots, one launch
+            cudaError_t e = launch_stage_layout(c, lin0, quad_slot(c, g * K), kb, c->copy_stream);
+            if (e != cudaSuccess) return cuda_fail(e, "quad/pair staging kernel");
         }
         RCT_CUDA(cudaEventRecord(c->ev_filled[g], c->copy_stream), "cudaEventRecord");
         RCT_CUDA(cudaStreamWaitEvent(s, c->ev_filled[g], 0), "cudaStreamWaitEvent");
@@ -1160,6 +1221,7 @@ rct_status backproject_host_impl(rct_ctx *c, const void *h_proj, int first_view,
                 p.z_count = std::min(slab, z_end - z);
                 cudaError_t e = launch(c, lc, p, s);
                 if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
+                if ((st = add_partials(c, z, p.z_count, s))) return st;
                 const size_t at = (size_t)(z - c->z_first) * plane;
                 RCT_CUDA(cudaEventRecord(c->ev_slab[i], s), "cudaEventRecord");
                 RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_slab[i], 0), "cudaStreamWaitEvent");
@@ -1174,6 +1236,7 @@ rct_status backproject_host_impl(rct_ctx *c, const void *h_proj, int first_view,
         } else {
             cudaError_t e = launch(c, lc, p, s);
             if (e != cudaSuccess) return cuda_fail(e, "backprojection launch");
+            if (b + kb >= n && (st = add_partials(c, c->z_first, c->z_count, s))) return st;
         }
         c->vol_zero_pending = false;
         RCT_CUDA(cudaEventRecord(c->ev_free[g], s), "cudaEventRecord");
@@ -1281,6 +1344,7 @@ rct_status rct_prepare(rct_ctx *c, int host_input) {
     if ((uses_tex(c) || uses_quad(c)) && (st = ensure_copy_machinery(c))) return st;
     if ((st = ensure_slots(c, 2 * c->tune.views_per_pass))) return st;
     if ((st = ensure_quads(c, 2 * c->tune.views_per_pass))) return st;
+    if ((st = ensure_parts(c))) return st;
     if (kernel_kind(c) == G_TEXLIN && c->dtype == DT_BF16 && (st = ensure_widen(c, (size_t)c->W * c->H))) return st;
     if (host_input && (st = ensure_host_staging(c))) return st;
     return RCT_OK;

@@ -310,15 +310,27 @@ __device__ __forceinline__ void block_frame(const ViewGeo *vg, float bX, float b
 // always takes the global frame (the texture unit needs absolute coordinates).
 // TRUNC: the cell index of Listing 1's (int) cast, which truncates toward zero, instead of floor
 // (RabbitCT compatibility; plain loads only).
-template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC>
+// SPLIT: the view split (see BpParams): this block handles one group of the pass's views and adds into
+// vol (group 0) or into its group's partial volume.
+template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC, bool SPLIT = false>
 __device__ __forceinline__ void bp_body(const BpParams &p) {
     static_assert(!FRAME || G == G_SOFT, "block frames are for the software gathers");
     static_assert(!TRUNC || (G == G_SOFT && ROUTE == ROUTE_LDG && !FRAME), "truncation: global frame, plain loads");
     static_assert(ROUTE != ROUTE_DQD || DT == DT_F32, "difference quads hold FP32 values");
+    static_assert(!SPLIT || (G == G_SOFT && !FRAME && !TRUNC), "view split: global frame, floor rule");
     const int L = p.L;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * XV;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z0 = p.z_base + blockIdx.z * R;
+    int group = 0, zblock = blockIdx.z;
+    if constexpr (SPLIT) {
+        group = blockIdx.z / p.split_runs;
+        zblock = blockIdx.z - group * p.split_runs;
+    }
+    const int z0 = p.z_base + zblock * R;
+    float *const vol = (SPLIT && group > 0) ? p.part + (group - 1) * p.part_stride : p.vol;
+    const int accumulate = (SPLIT && group > 0) ? p.accumulate_part : p.accumulate;
+    const int k_begin = SPLIT ? group * p.split_views : 0;
+    const int k_end = SPLIT ? min(k_begin + p.split_views, p.K) : p.K;
     // the block's first voxel (centred coordinates, exact) and this thread's offset from it
     const float bX = static_cast<float>(blockIdx.x * blockDim.x * XV) - p.cen;
     const float bY = static_cast<float>(blockIdx.y * blockDim.y) - p.cen;
@@ -328,10 +340,10 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
 
     const bool inside = x0 < L && y < L;
     const size_t plane = static_cast<size_t>(L) * L;
-    float *vb = p.vol + (inside ? static_cast<size_t>(z0) * plane + static_cast<size_t>(y) * L + x0 : 0);
+    float *vb = vol + (inside ? static_cast<size_t>(z0) * plane + static_cast<size_t>(y) * L + x0 : 0);
     // The volume rows of the run are requested into L2 first (without holding registers), so the
     // DRAM latency overlaps the set-up below.
-    if (inside && p.accumulate) {
+    if (inside && accumulate) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
             if (z0 + r < L) asm volatile("prefetch.global.L2 [%0];" :: "l"(vb + r * plane));
@@ -352,7 +364,7 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
     float acc[R][XV];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        bool live = p.accumulate && (z0 + r < L);
+        bool live = accumulate && (z0 + r < L);
 #ifdef RCT_CHECK_BOUNDS
         {
             const long long at = static_cast<long long>(z0 + r - p.vol_z0) * L * L + static_cast<long long>(y) * L + x0;
@@ -377,7 +389,7 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
     const int tex_zrun = p.tex_zrun;   // z positions [0, tex_zrun) use the texture route
 
 #pragma unroll 1
-    for (int k = 0; k < p.K; ++k) {
+    for (int k = k_begin; k < k_end; ++k) {
         const ViewParams &v = p.view[k];
         const float2 *muv = reinterpret_cast<const float2 *>(v.muv);
         const float *mw = v.mw;
@@ -505,9 +517,9 @@ __device__ __forceinline__ void bp_body(const BpParams &p) {
     }
 }
 
-template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = false>
+template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = false, bool SPLIT = false>
 __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParams p) {
-    bp_body<G, DT, XV, R, ROUTE, FRAME, TRUNC>(p);
+    bp_body<G, DT, XV, R, ROUTE, FRAME, TRUNC, SPLIT>(p);
 }
 
 // Register caps (measured): the block-frame kernels keep the frame's rows and shift in per-thread
@@ -522,17 +534,28 @@ __global__ void __maxnreg__(RCT_CAPPED_MAXREG) bp_kernel_frame(const __grid_cons
     bp_body<G_SOFT, DT, XV, R, ROUTE, true, false>(p);
 }
 
-template <int G, int DT, int XV, int ROUTE, bool TRUNC>
+template <int G, int DT, int XV, int ROUTE, bool TRUNC, bool SPLIT = false>
 __global__ void __maxnreg__(RCT_CAPPED_MAXREG) bp_kernel_r16(const __grid_constant__ BpParams p) {
-    bp_body<G, DT, XV, 16, ROUTE, false, TRUNC>(p);
+    bp_body<G, DT, XV, 16, ROUTE, false, TRUNC, SPLIT>(p);
 }
 
-template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = false>
+template <int G, int DT, int XV, int R, int ROUTE, bool FRAME, bool TRUNC = false, bool SPLIT = false>
 cudaError_t launch_one(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     if (FRAME && !p.geo) return cudaErrorInvalidValue;
     const int gx = (p.L / XV + c.bx - 1) / c.bx;
     const int zc = p.z_count > 0 ? p.z_count : p.L;
-    const dim3 grid(gx, (p.L + c.by - 1) / c.by, (zc + R - 1) / R);
+    const int runs = (zc + R - 1) / R;
+    if constexpr (SPLIT) {
+        if (c.split < 2 || !p.part) return cudaErrorInvalidValue;
+        BpParams q = p;
+        q.split_runs = runs;
+        q.split_views = (p.K + c.split - 1) / c.split;
+        const dim3 grid(gx, (p.L + c.by - 1) / c.by, runs * c.split);
+        if constexpr (R == 16) bp_kernel_r16<G, DT, XV, ROUTE, false, true><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(q);
+        else bp_kernel<G, DT, XV, R, ROUTE, false, false, true><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(q);
+        return cudaGetLastError();
+    }
+    const dim3 grid(gx, (p.L + c.by - 1) / c.by, runs);
     if constexpr (FRAME) {
         bp_kernel_frame<DT, XV, R, ROUTE><<<grid, dim3(c.bx, c.by, 1), 0, s>>>(p);
     } else if constexpr (R == 16) {
@@ -543,15 +566,15 @@ cudaError_t launch_one(const LaunchConfig &c, const BpParams &p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int G, int DT, int XV, int ROUTE, bool FRAME, bool TRUNC = false>
+template <int G, int DT, int XV, int ROUTE, bool FRAME, bool TRUNC = false, bool SPLIT = false>
 cudaError_t dispatch_r(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     switch (c.zrun) {
-        case 1: return launch_one<G, DT, XV, 1, ROUTE, FRAME, TRUNC>(c, p, s);
-        case 2: return launch_one<G, DT, XV, 2, ROUTE, FRAME, TRUNC>(c, p, s);
-        case 4: return launch_one<G, DT, XV, 4, ROUTE, FRAME, TRUNC>(c, p, s);
-        case 8: return launch_one<G, DT, XV, 8, ROUTE, FRAME, TRUNC>(c, p, s);
+        case 1: return launch_one<G, DT, XV, 1, ROUTE, FRAME, TRUNC, SPLIT>(c, p, s);
+        case 2: return launch_one<G, DT, XV, 2, ROUTE, FRAME, TRUNC, SPLIT>(c, p, s);
+        case 4: return launch_one<G, DT, XV, 4, ROUTE, FRAME, TRUNC, SPLIT>(c, p, s);
+        case 8: return launch_one<G, DT, XV, 8, ROUTE, FRAME, TRUNC, SPLIT>(c, p, s);
         case 16:
-            if constexpr (XV <= 2) return launch_one<G, DT, XV, 16, ROUTE, FRAME, TRUNC>(c, p, s);
+            if constexpr (XV <= 2) return launch_one<G, DT, XV, 16, ROUTE, FRAME, TRUNC, SPLIT>(c, p, s);
             return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
@@ -562,6 +585,17 @@ template <int G, int DT, int ROUTE>
 cudaError_t dispatch_xv(const LaunchConfig &c, const BpParams &p, cudaStream_t s) {
     constexpr bool kFrames = (G == G_SOFT && DT == DT_F32);
     if ((c.frame && !kFrames) || c.trunc) return cudaErrorInvalidValue;
+    if (c.split > 1) {
+        if (G != G_SOFT || c.frame) return cudaErrorInvalidValue;
+        if constexpr (G == G_SOFT) {
+            switch (c.xv) {
+                case 1: return dispatch_r<G, DT, 1, ROUTE, false, false, true>(c, p, s);
+                case 2: return dispatch_r<G, DT, 2, ROUTE, false, false, true>(c, p, s);
+                case 4: return dispatch_r<G, DT, 4, ROUTE, false, false, true>(c, p, s);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+    }
     switch (c.xv) {
         case 1: return c.frame ? dispatch_r<G, DT, 1, ROUTE, kFrames>(c, p, s) : dispatch_r<G, DT, 1, ROUTE, false>(c, p, s);
         case 2: return c.frame ? dispatch_r<G, DT, 2, ROUTE, kFrames>(c, p, s) : dispatch_r<G, DT, 2, ROUTE, false>(c, p, s);

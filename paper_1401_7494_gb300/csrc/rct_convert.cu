@@ -37,6 +37,17 @@ __global__ void narrow_kernel(const float *__restrict__ src, unsigned short *__r
     }
 }
 
+// vol[i] += part[i] + part[stride + i] + ... in that order (the view split's partial volumes).
+__global__ void add_partials_kernel(float *__restrict__ vol, const float *__restrict__ part, size_t n, size_t stride,
+                                    int parts) {
+    const size_t step = static_cast<size_t>(gridDim.x) * blockDim.x;
+    for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += step) {
+        float v = vol[i];
+        for (int k = 0; k < parts; ++k) v += part[k * stride + i];
+        vol[i] = v;
+    }
+}
+
 __global__ void widen_bf16_kernel(const unsigned short *__restrict__ src, float *__restrict__ dst, size_t n) {
     const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
     for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
@@ -67,6 +78,13 @@ cudaError_t launch_convert(const float *src, void *dst, size_t n, int dtype, cud
     return cudaGetLastError();
 }
 
+cudaError_t launch_add_partials(float *vol, const float *part, size_t n, size_t stride, int parts, cudaStream_t s) {
+    if (n == 0 || parts <= 0) return cudaSuccess;
+    const int block = 256;
+    add_partials_kernel<<<grid_for(n, block), block, 0, s>>>(vol, part, n, stride, parts);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_widen_bf16(const uint16_t *src, float *dst, size_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int block = 256;
@@ -86,8 +104,16 @@ __device__ __forceinline__ T px_or_zero(const T *img, int W, int H, int i, int j
                ? img[static_cast<size_t>(j) * W + i] : T(0);
 }
 
+// The staging kernels below take one view per blockIdx.z: view z reads img + z * W * H and writes its
+// layout at q + z * (elements of one staged image), so a batch of views that sit next to each other in
+// memory, and go to consecutive staging slots, is staged by one launch.
+#define RCT_VIEW_OFFSETS(ELEMS)                                                  \
+    img += static_cast<size_t>(blockIdx.z) * W * H;                             \
+    q += static_cast<size_t>(blockIdx.z) * (ELEMS);
+
 // One thread per padded element (jy, ix): gathers the 2x2 cell with corner (ix - 1, jy - 1).
 __global__ void stage_quads_f32(const float *__restrict__ img, float4 *__restrict__ q, int W, int H) {
+    RCT_VIEW_OFFSETS(static_cast<size_t>(W + 1) * (H + 1))
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int jy = blockIdx.y;
     if (ix > W) return;
@@ -98,6 +124,7 @@ __global__ void stage_quads_f32(const float *__restrict__ img, float4 *__restric
 }
 
 __global__ void stage_quads_u16(const unsigned short *__restrict__ img, uint2 *__restrict__ q, int W, int H) {
+    RCT_VIEW_OFFSETS(static_cast<size_t>(W + 1) * (H + 1))
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int jy = blockIdx.y;
     if (ix > W) return;
@@ -109,6 +136,7 @@ __global__ void stage_quads_u16(const unsigned short *__restrict__ img, uint2 *_
 
 // One thread per padded pair (jy, ix): (I[jy-1][ix-1], I[jy][ix-1]), zero off the image.
 __global__ void stage_pairs_f32(const float *__restrict__ img, float2 *__restrict__ q, int W, int H) {
+    RCT_VIEW_OFFSETS(static_cast<size_t>(W + 2) * (H + 1))
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int jy = blockIdx.y;
     if (ix > W + 1) return;
@@ -117,6 +145,7 @@ __global__ void stage_pairs_f32(const float *__restrict__ img, float2 *__restric
 }
 
 __global__ void stage_pairs_u16(const unsigned short *__restrict__ img, unsigned *__restrict__ q, int W, int H) {
+    RCT_VIEW_OFFSETS(static_cast<size_t>(W + 2) * (H + 1))
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int jy = blockIdx.y;
     if (ix > W + 1) return;
@@ -127,6 +156,7 @@ __global__ void stage_pairs_u16(const unsigned short *__restrict__ img, unsigned
 // One thread per padded element (jy, ix): the cell with corner (ix - 1, jy - 1) as (a, c, b - a, d - c),
 // a = I[j0][i0], c = I[j0+1][i0], b = I[j0][i0+1], d = I[j0+1][i0+1], zero off the image.
 __global__ void stage_dquads_f32(const float *__restrict__ img, float4 *__restrict__ q, int W, int H) {
+    RCT_VIEW_OFFSETS(static_cast<size_t>(W + 1) * (H + 1))
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int jy = blockIdx.y;
     if (ix > W) return;
@@ -138,8 +168,9 @@ __global__ void stage_dquads_f32(const float *__restrict__ img, float4 *__restri
 
 }  // namespace
 
-cudaError_t launch_stage_dquads(const float *src, void *dst, int W, int H, cudaStream_t s) {
-    const dim3 block(256), grid((W + 1 + 255) / 256, H + 1);
+cudaError_t launch_stage_dquads(const float *src, void *dst, int W, int H, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const dim3 block(256), grid((W + 1 + 255) / 256, H + 1, n);
     stage_dquads_f32<<<grid, block, 0, s>>>(src, static_cast<float4 *>(dst), W, H);
     return cudaGetLastError();
 }
@@ -148,8 +179,9 @@ size_t pair_bytes(int W, int H, int dtype) {
     return static_cast<size_t>(W + 2) * (H + 1) * (dtype == DT_F32 ? 8 : 4);
 }
 
-cudaError_t launch_stage_pairs(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s) {
-    const dim3 block(256), grid((W + 2 + 255) / 256, H + 1);
+cudaError_t launch_stage_pairs(const void *src, void *dst, int W, int H, int dtype, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const dim3 block(256), grid((W + 2 + 255) / 256, H + 1, n);
     if (dtype == DT_F32)
         stage_pairs_f32<<<grid, block, 0, s>>>(static_cast<const float *>(src), static_cast<float2 *>(dst), W, H);
     else
@@ -161,8 +193,9 @@ size_t quad_bytes(int W, int H, int dtype) {
     return static_cast<size_t>(W + 1) * (H + 1) * (dtype == DT_F32 ? 16 : 8);
 }
 
-cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s) {
-    const dim3 block(256), grid((W + 1 + 255) / 256, H + 1);
+cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dtype, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const dim3 block(256), grid((W + 1 + 255) / 256, H + 1, n);
     if (dtype == DT_F32)
         stage_quads_f32<<<grid, block, 0, s>>>(static_cast<const float *>(src), static_cast<float4 *>(dst), W, H);
     else

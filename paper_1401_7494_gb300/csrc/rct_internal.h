@@ -84,6 +84,15 @@ struct BpParams {
 #endif
     unsigned long long *viol;  // bounds-checking build: violation counter on the device (null: not counted)
     ViewParams view[KMAX];
+    // View split (kernels compiled with SPLIT only): the pass's views are dealt out in contiguous groups of
+    // split_views to `splits` groups of blocks; group 0 adds into vol, group s > 0 into the partial volume
+    // part + (s - 1) * part_stride (addressed like vol), written when accumulate_part is 0.  blockIdx.z =
+    // group * split_runs + z-run.  The partials are added into vol after the call's last pass.
+    float *part;
+    long long part_stride;
+    int split_runs;
+    int split_views;
+    int accumulate_part;
 };
 
 struct LaunchConfig {
@@ -94,6 +103,7 @@ struct LaunchConfig {
     int bx, by;  // block shape
     int frame;   // 1: block frames (FP32 software gathers only; BpParams::geo set)
     int trunc;   // 1: Listing 1's truncating cell index (FP32, plain loads, global frame)
+    int split;   // groups of the view split (1: none; global frame, floor rule, software gathers only)
 };
 
 // Kernel launchers (one translation unit per gather kind).
@@ -116,13 +126,15 @@ cudaError_t launch_ramp_filter(const FilterParams &f, const float *raw, void *ou
                                cudaStream_t s);
 
 cudaError_t launch_convert(const float *src, void *dst, size_t n, int dtype, cudaStream_t s);
-// Build the zero-padded quad image of one view (see ViewParams) from its linear image.
-cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s);
+// Build the zero-padded quad images of n views (see ViewParams) from their linear images: view k reads
+// src + k * W * H elements and writes the staged image k images after dst (one launch per batch).
+cudaError_t launch_stage_quads(const void *src, void *dst, int W, int H, int dtype, int n, cudaStream_t s);
 size_t quad_bytes(int W, int H, int dtype);
-// Build the zero-padded vertical-pair image of one view (see ViewParams).
-cudaError_t launch_stage_pairs(const void *src, void *dst, int W, int H, int dtype, cudaStream_t s);
-// Build the zero-padded difference-quad image of one FP32 view (see ViewParams); quad_bytes(W, H, DT_F32).
-cudaError_t launch_stage_dquads(const float *src, void *dst, int W, int H, cudaStream_t s);
+// Build the zero-padded vertical-pair images of n views (see ViewParams), laid out as above.
+cudaError_t launch_stage_pairs(const void *src, void *dst, int W, int H, int dtype, int n, cudaStream_t s);
+// Build the zero-padded difference-quad images of n FP32 views (see ViewParams; quad_bytes(W, H, DT_F32)
+// each), laid out as above.
+cudaError_t launch_stage_dquads(const float *src, void *dst, int W, int H, int n, cudaStream_t s);
 size_t pair_bytes(int W, int H, int dtype);
 
 // Fill the matrix of a view (FP32) from its FP64 fold (rows u', v', w over centred voxel
@@ -133,5 +145,7 @@ void set_view_geo(ViewGeo *vg, const double fold[12], int cu, int cv);
 // Record a message for rct_last_error() on the calling thread and return `code`.
 rct_status rct_internal_fail(rct_status code, const char *fmt, ...);
 cudaError_t launch_widen_bf16(const uint16_t *src, float *dst, size_t n, cudaStream_t s);
+// vol[i] += part[i] + part[stride + i] + ... (parts terms, in that order) for i < n.
+cudaError_t launch_add_partials(float *vol, const float *part, size_t n, size_t stride, int parts, cudaStream_t s);
 
 }  // namespace rct

@@ -37,7 +37,7 @@ class RctError(RuntimeError):
 class rct_tuning(ctypes.Structure):
     _fields_ = [("views_per_pass", ctypes.c_int), ("zrun", ctypes.c_int), ("xvec", ctypes.c_int),
                 ("block_x", ctypes.c_int), ("block_y", ctypes.c_int), ("gather", ctypes.c_int),
-                ("tex_zrun", ctypes.c_int)]
+                ("tex_zrun", ctypes.c_int), ("view_split", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -314,8 +314,9 @@ def rct_set_geometry_rabbitct(ctx, matrices_colmajor, O: float, MM: float) -> No
                                            ctypes.c_float(O), ctypes.c_float(MM)))
 
 
-def rct_set_tuning(ctx, views_per_pass=0, zrun=0, xvec=0, block_x=0, block_y=0, gather=0, tex_zrun=0) -> None:
-    t = rct_tuning(views_per_pass, zrun, xvec, block_x, block_y, gather, tex_zrun)
+def rct_set_tuning(ctx, views_per_pass=0, zrun=0, xvec=0, block_x=0, block_y=0, gather=0, tex_zrun=0,
+                   view_split=0) -> None:
+    t = rct_tuning(views_per_pass, zrun, xvec, block_x, block_y, gather, tex_zrun, view_split)
     _check(lib().rct_set_tuning(ctx, ctypes.byref(t)))
 
 

@@ -47,6 +47,9 @@ TUNINGS = [
     dict(gather=rct.RCT_GATHER_DQUAD, views_per_pass=24, zrun=8, xvec=1, block_x=8, block_y=16),
     dict(gather=rct.RCT_GATHER_DQUAD, views_per_pass=7, zrun=16, xvec=2, block_x=16, block_y=8),
     dict(gather=rct.RCT_GATHER_DQUAD, views_per_pass=13, zrun=2, xvec=4, block_x=8, block_y=8),
+    dict(gather=rct.RCT_GATHER_LDG, views_per_pass=32, zrun=4, xvec=1, block_x=8, block_y=16, view_split=4),
+    dict(gather=rct.RCT_GATHER_PAIR, views_per_pass=7, zrun=16, xvec=2, block_x=8, block_y=16, view_split=8),
+    dict(gather=rct.RCT_GATHER_TLD4, views_per_pass=9, zrun=2, xvec=1, block_x=16, block_y=8, view_split=2),
 ]
 
 
@@ -529,3 +532,40 @@ def test_difference_quads_need_fp32(small_cases):
         with pytest.raises(rct.RctError) as e:
             bp.backproject(data, 0, w.n_views)
         assert e.value.status == rct.RCT_ENOTSUP
+
+
+@pytest.mark.parametrize("split", [2, 4, 8])
+def test_view_split_is_deterministic_and_close_to_the_plain_order(small_cases, cuda_device, split):
+    """The view split regroups each voxel's sum (its groups' partial volumes are added after the call): two runs
+    give the same bits, split calls and the host path with the overlapped read-back agree with the oracle, and
+    the plain order is within rounding."""
+    w, proj, host = small_cases["L40"]
+    t = dict(gather=rct.RCT_GATHER_LDG, views_per_pass=11, zrun=4, xvec=1, block_x=8, block_y=16)
+    plain = gpu_backproject(w, proj, tuning=t)
+    a = gpu_backproject(w, proj, tuning=dict(t, view_split=split))
+    b = gpu_backproject(w, proj, tuning=dict(t, view_split=split))
+    assert np.array_equal(a, b)
+    ref = oracle_volume(w, host)
+    assert_parity(a, ref, f"view split {split}")
+    assert rel_errors(a, plain)[0] < 1e-6
+    chunks = gpu_backproject(w, proj, tuning=dict(t, view_split=split), chunks=[(0, 5), (5, 18), (18, w.n_views)])
+    assert_parity(chunks, ref, f"view split {split}, three calls")
+    stream = torch.cuda.current_stream()
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(**dict(t, view_split=split))
+        out = torch.empty((w.L,) * 3, dtype=torch.float32, pin_memory=True)
+        bp.backproject_host_read(proj.cpu().pin_memory(), out, 0, w.n_views, stream)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.numpy(), a)                 # same passes, same groups: same bits
+
+
+def test_view_split_needs_the_global_frame(small_cases):
+    w, proj, _ = small_cases["L37"]
+    with rct.Backprojector(w.L, w.geom.det_w, w.geom.det_h, w.n_views) as bp:
+        bp.set_geometry(w.geom.matrices, w.origin, w.spacing).set_tuning(view_split=4)
+        bp.set_frame(rct.RCT_FRAME_BLOCK)
+        with pytest.raises(rct.RctError) as e:
+            bp.backproject(proj, 0, w.n_views)
+        assert e.value.status == rct.RCT_ENOTSUP
+        with pytest.raises(rct.RctError):
+            bp.set_tuning(view_split=3)

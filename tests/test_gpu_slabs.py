@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 TUNES = [dict(gather=rct.RCT_GATHER_PAIR, views_per_pass=16, zrun=8, xvec=1, block_x=8, block_y=16),
          dict(gather=rct.RCT_GATHER_PAIR, views_per_pass=9, zrun=16, xvec=1, block_x=8, block_y=16),
          dict(gather=rct.RCT_GATHER_TLD4, views_per_pass=7, zrun=4, xvec=2, block_x=16, block_y=8),
-         dict(gather=rct.RCT_GATHER_LDG, views_per_pass=32, zrun=2, xvec=1, block_x=32, block_y=4)]
+         dict(gather=rct.RCT_GATHER_LDG, views_per_pass=32, zrun=2, xvec=1, block_x=32, block_y=4),
+         dict(gather=rct.RCT_GATHER_LDG, views_per_pass=12, zrun=4, xvec=1, block_x=8, block_y=16, view_split=4)]
 
 
 @pytest.fixture(scope="module")
