@@ -84,7 +84,7 @@ def run_mode(mode: str, protocols, host, *, n_requests=200, load=0.7, views_per_
     rate = load / svc
     reqs = serving.poisson_requests(n_requests, rate, PROTOCOL_VIEWS, seed=seed, L_choices=L_CHOICES,
                                     L_weights=L_WEIGHTS, mode=mode, views_per_s=views_per_s, raw=raw)
-    ex = serving.GpuExecutor(protocols, host, use_graphs=use_graphs)
+    ex = serving.GpuExecutor(protocols, host, use_graphs=use_graphs, timeline=True)
     sch = serving.Scheduler(ex, int(budget_gb * (1 << 30)), max_active=max_active)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -100,6 +100,9 @@ def run_mode(mode: str, protocols, host, *, n_requests=200, load=0.7, views_per_
                 "views_per_s": views_per_s, "graph_captures": ex.captures, "graph_launches": ex.graph_launches,
                 "peak_concurrent_requests": peak, "offered_updates": sum(r.updates for r in reqs),
                 "span_s": reqs[-1].arrival})
+    # device evidence of overlap: CUDA-event intervals of every chunk's work on its request's stream
+    ov = serving.overlap_stats(ex.device_timeline())
+    out["device_overlap"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in ov.items()}
     ex.close()
     log(json.dumps(out))
     return out

@@ -296,7 +296,7 @@ class GpuExecutor:
     """
 
     def __init__(self, protocols: dict[str, Protocol_], host_data: dict, *, use_graphs: bool = True,
-                 tuning_fn=None, device: int = 0):
+                 tuning_fn=None, device: int = 0, timeline: bool = False):
         import torch
         from . import rct, tuning
         self.torch = torch
@@ -309,6 +309,22 @@ class GpuExecutor:
         self.free_slots: dict[tuple, list[_Slot]] = collections.defaultdict(list)
         self.graph_launches = 0
         self.captures = 0
+        # Device timeline (optional): timing events around every chunk's work on its request's stream, so the
+        # device intervals of different requests' work can be compared after the run (device_timeline()).
+        self.timeline = False
+        self._marks: list = []
+        self._t0 = None
+        if timeline:
+            self.start_timeline()
+
+    def start_timeline(self) -> None:
+        """Start (or restart) recording the device timeline; earlier records are dropped."""
+        torch = self.torch
+        torch.cuda.synchronize(self.device)
+        self.timeline = True
+        self._marks = []
+        self._t0 = torch.cuda.Event(enable_timing=True)
+        self._t0.record(torch.cuda.current_stream(self.device))
 
     # -- sizing
     def _key(self, r: Request) -> tuple:
@@ -417,6 +433,9 @@ class GpuExecutor:
         torch = self.torch
         a, b = h.req.chunk_range(c)
         s = h.slot
+        if self.timeline:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
         with torch.cuda.stream(s.stream):
             s.d_chunk[:b - a].copy_(h.host[a:b], non_blocking=True)
         if self.use_graphs:
@@ -424,6 +443,15 @@ class GpuExecutor:
             self.graph_launches += 1
         else:
             self._chunk_work(s, h.req, c)
+        if self.timeline:
+            e1.record(s.stream)
+            self._marks.append((h.req.rid, c, e0, e1))
+
+    def device_timeline(self) -> list[tuple[int, int, float, float]]:
+        """(request id, chunk, start ms, end ms) of every chunk's device work since the executor was made: from
+        the moment its stream reached the chunk's copy to the end of its pass (call after the work is done)."""
+        self.torch.cuda.synchronize(self.device)
+        return [(rid, c, self._t0.elapsed_time(e0), self._t0.elapsed_time(e1)) for rid, c, e0, e1 in self._marks]
 
     def seal(self, h: _Handle) -> None:
         h.slot.done_event = self.torch.cuda.Event()
@@ -458,3 +486,30 @@ class GpuExecutor:
             for s in lst:
                 self._destroy(s)
         self.free_slots.clear()
+
+
+def overlap_stats(intervals: list[tuple[int, int, float, float]]) -> dict:
+    """From (request id, chunk, start, end) device intervals: the time some request's work was in flight, the
+    time at least two different requests' work was, and the largest number of requests in flight at once."""
+    events = []
+    for rid, _, a, b in intervals:
+        if b > a:
+            events.append((a, 1, rid))
+            events.append((b, -1, rid))
+    events.sort(key=lambda e: (e[0], e[1]))
+    live: dict[int, int] = collections.Counter()
+    busy = multi = 0.0
+    peak = 0
+    last = None
+    for t, d, rid in events:
+        if last is not None:
+            n = sum(1 for v in live.values() if v > 0)
+            if n >= 1:
+                busy += t - last
+            if n >= 2:
+                multi += t - last
+        live[rid] += d
+        peak = max(peak, sum(1 for v in live.values() if v > 0))
+        last = t
+    return {"busy_ms": busy, "overlap_ms": multi, "overlap_fraction": (multi / busy) if busy else 0.0,
+            "peak_requests_in_flight": peak}

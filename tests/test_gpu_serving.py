@@ -110,3 +110,24 @@ def test_raw_ingest_needs_filter_geometry(setup):
     host2 = dict(host, **{"pX/raw": host["pA/raw"]})
     res, _ = _serve(bare, host2, [_req(0, 24, "pX", 24, 0.0, raw=True)])
     assert res[0].status == "error"
+
+
+def test_concurrent_requests_overlap_on_the_device(setup, cuda_device):
+    """Continuous batching puts different requests' work on the device at the same time: once the requests'
+    slots exist (a first batch of the same shapes), the CUDA-event intervals of the chunks' work on their
+    requests' streams overlap for a good part of the busy time."""
+    protos, host, _ = setup
+    shapes = [(128, "pB", 40), (128, "pB", 40), (96, "pA", 24), (128, "pB", 40), (96, "pA", 24), (128, "pB", 40)]
+    ex = serving.GpuExecutor(protos, host, use_graphs=True)
+    sch = serving.Scheduler(ex, 8 << 30, max_active=8)
+    warm = sch.run([_req(i, L, p, n, 0.0, "f32") for i, (L, p, n) in enumerate(shapes)])
+    assert all(r.status == "ok" for r in warm)
+    ex.start_timeline()
+    reqs = [_req(10 + i, L, p, n, 0.0, "f32") for i, (L, p, n) in enumerate(shapes)]
+    res = serving.Scheduler(ex, 8 << 30, max_active=8).run(reqs)
+    tl = ex.device_timeline()
+    ex.close()
+    assert all(r.status == "ok" for r in res)
+    assert len(tl) == sum(q.n_chunks for q in reqs) and all(b >= a for _, _, a, b in tl)
+    st = serving.overlap_stats(tl)
+    assert st["peak_requests_in_flight"] >= 3 and st["overlap_fraction"] > 0.5, st

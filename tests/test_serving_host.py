@@ -179,3 +179,14 @@ def test_schedule_is_deterministic():
     a = run(reqs)[2].log
     b = run(reqs)[2].log
     assert a == b
+
+
+def test_overlap_stats_counts_time_with_two_requests_in_flight():
+    from paper_1401_7494_gb300 import serving
+    iv = [(1, 0, 0.0, 10.0), (1, 1, 10.0, 20.0), (2, 0, 5.0, 12.0), (3, 0, 30.0, 35.0), (2, 1, 12.0, 15.0)]
+    st = serving.overlap_stats(iv)
+    assert st["busy_ms"] == 25.0                   # [0, 20] and [30, 35]
+    assert st["overlap_ms"] == 10.0                # [5, 15]: requests 1 and 2
+    assert st["peak_requests_in_flight"] == 2
+    assert abs(st["overlap_fraction"] - 0.4) < 1e-12
+    assert serving.overlap_stats([])["busy_ms"] == 0.0
