@@ -389,6 +389,42 @@ def live_warp_fraction(w, tun: dict, n_warps: int = 3000, n_views: int = 24, see
     return live / max(total, 1)
 
 
+def warp_footprints(w, tun: dict, n_views: int = 8) -> list:
+    """Projected lane offsets of one warp of the kernel's block (the 32 threads with the lowest ids of a block at
+    the volume centre, its first z-run voxel), for n_views views spread over the scan: (32 x 2 offsets in pixels
+    from lane 0, the step of lane 0 to the next voxel of the run), from the geometry in FP64."""
+    L, bx, xv = w.L, tun["block_x"], tun["xvec"]
+    lane = np.arange(32)
+    x = (lane % bx) * xv + (L // 2 // (bx * xv)) * bx * xv
+    y = lane // bx + L // 2
+    zc = L // 2
+    out = []
+    for k in np.linspace(0, w.n_views - 1, n_views).round().astype(int):
+        def uv(z):
+            X = np.stack([w.origin[0] + x * w.spacing[0], w.origin[1] + y * w.spacing[1],
+                          np.full(32, w.origin[2] + z * w.spacing[2]), np.ones(32)], axis=1)
+            q = X @ w.geom.matrices[k].T
+            return q[:, 0] / q[:, 2], q[:, 1] / q[:, 2]
+        u0, v0 = uv(zc)
+        u1, v1 = uv(zc + 1)
+        off = np.stack([u0 - u0[0], v0 - v0[0]], axis=1)
+        out.append((off, float(u1[0] - u0[0]), float(v1[0] - v0[0])))
+    return out
+
+
+def pattern_ceiling(w, tun: dict) -> float | None:
+    """Mean over the footprints of warp_footprints of the plain-load gather's measured rate (cells per second)
+    for that footprint, or None where a footprint exceeds the probe's limits."""
+    from paper_1401_7494_gb300 import probes, rct
+    rates = []
+    for off, su, sv in warp_footprints(w, tun):
+        try:
+            rates.append(probes.rct_probe_gather_pattern(off, su, sv, 1024))
+        except rct.RctError:
+            return None
+    return float(np.mean(rates)) if rates else None
+
+
 def k_sweep(dev, stream, peaks: dict) -> dict:
     """Views per pass K against the volume stream at L = 1024 x 496: the volume is read and written once per
     pass (8/K bytes of HBM per voxel update), so small K is HBM-bound and large K fetch-bound."""
@@ -564,6 +600,20 @@ def run_ours(args, dist: Dist) -> dict | None:
                 "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                         "frac": round(achieved_gbs / hbm_peak, 4), "algorithmic_bytes_per_launch": int(bytes_per_launch),
                         "peak_source": "measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "fallback"}}
+    if route == "ldg" and args.dtype == "f32":
+        # Plain loads of four 4-byte taps: where lanes land far apart (L=128: 10 px) the L1 data pipe's
+        # wavefronts, not its bytes, bind.  The ceiling of this access pattern is measured by replaying the
+        # kernel's own warp footprints (projected from the geometry) in an L1-resident image; the cells the
+        # kernel fetches are the updates of warps the clip test keeps.
+        pc = pattern_ceiling(w, tun)
+        if pc:
+            cells = kernel_gups * live                                # G cells/s
+            roofline["gather_pattern"] = {
+                "achieved": round(cells, 1), "peak": round(pc / 1e9, 1), "unit": "Gcell/s",
+                "frac": round(cells / (pc / 1e9), 4),
+                "what": "cells gathered (four 4-byte loads each) by warps the clip test keeps",
+                "peak_source": "measured in this run: rct_probe_gather_pattern with the kernel's warp footprint "
+                               "at 8 views of the scan (mean)"}
     if tex_view is not None:
         # the texture route's gathers go through the texture pipe, not the load data path: its issued-gather
         # rate against the measured tld4 rate is the headline figure; the byte view moves to a sub-object

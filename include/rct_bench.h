@@ -57,6 +57,19 @@ RCT_API rct_status rct_probe_l1_bandwidth(int iters, double *rate);
  */
 RCT_API rct_status rct_probe_l2_sectors(int iters, double *rate);
 
+/*
+ * Cells per second for the backprojection's plain-load gather (four 4-byte
+ * taps of a 2x2 cell per lane) with a given warp footprint: lane l fetches
+ * at (x + lane_uv[2l], y + lane_uv[2l + 1]) pixels from an L1-resident
+ * 256 x 128 FP32 image, and every fetch moves the footprint by (step_u,
+ * step_v), as the next voxel of a z-run does.  The caller passes a real
+ * warp's projected voxel offsets, so the rate is the ceiling of that access
+ * pattern.  Offsets within +-100 px, the rows they span within 40 px, steps
+ * within +-16 px, iters >= 16; RCT_EINVAL otherwise.
+ */
+RCT_API rct_status rct_probe_gather_pattern(const float *lane_uv, float step_u, float step_v, int iters,
+                                            double *rate);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,37 @@ __global__ void __launch_bounds__(256) ldg4_probe_kernel(const float *__restrict
     if (acc == 1.2345e-30f) sink[0] = acc;
 }
 
+// The backprojection's plain-load gather with a given warp footprint: lane l fetches the 2x2 cell at
+// (x + du[l], y + dv[l]) with four 4-byte loads from a 256 x 128 FP32 image (128 KiB: L1 resident), and
+// every fetch moves the warp's footprint by (step_u, step_v), as the next voxel of a z-run does.  Offsets
+// come from the caller (a real warp's projected voxels), so the rate is that access pattern's ceiling.
+constexpr int kPatW = 256, kPatH = 128;
+
+__global__ void __launch_bounds__(256) pattern_probe_kernel(const float *__restrict__ img, const float2 *__restrict__ duv,
+                                                            int iters, float step_u, float step_v, float *sink) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const float2 o = duv[lane];
+    float x = 16.0f + o.x + (warp & 15) * 2.0f;
+    float y = 8.0f + o.y + ((warp >> 4) & 15) * 1.0f;
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+        const int i0 = __float2int_rd(x), j0 = __float2int_rd(y);
+        const bool ok = static_cast<unsigned>(i0) < static_cast<unsigned>(kPatW - 1) &&
+                        static_cast<unsigned>(j0) < static_cast<unsigned>(kPatH - 1);
+        const float *r0 = img + j0 * kPatW + i0;
+        const float a = ok ? __ldg(r0) : 0.f, b = ok ? __ldg(r0 + 1) : 0.f;
+        const float c = ok ? __ldg(r0 + kPatW) : 0.f, d = ok ? __ldg(r0 + kPatW + 1) : 0.f;
+        acc += (a + b) + (c + d);
+        x += step_u;
+        y += step_v;
+        x = (x > kPatW - 24.0f) ? x - (kPatW - 48.0f) : (x < 24.0f ? x + (kPatW - 48.0f) : x);
+        y = (y > kPatH - 12.0f) ? y - (kPatH - 24.0f) : (y < 12.0f ? y + (kPatH - 24.0f) : y);
+    }
+    if (acc == 1.2345e-30f) sink[0] = acc;
+}
+
 // Staged-layout loads over a detector-sized buffer (larger than L1, resident in L2): one 16-byte
 // quad (PAIRS = false) or two consecutive 8-byte pairs (PAIRS = true) per fetch, same lane layout.
 constexpr int kLayoutW = 1280, kLayoutH = 1024;
@@ -217,6 +248,61 @@ RCT_API rct_status rct_probe_texture(int mode, int dtype, float stride_px, float
     if (tex) cudaDestroyTextureObject(tex);
     if (arr) cudaFreeArray(arr);
     if (sink) cudaFree(sink);
+    return st;
+}
+
+RCT_API rct_status rct_probe_gather_pattern(const float *lane_uv, float step_u, float step_v, int iters,
+                                            double *rate) {
+    if (!rate || !lane_uv || iters < 16) return RCT_EINVAL;
+    for (int l = 0; l < 64; ++l)
+        if (!(lane_uv[l] >= -100.0f && lane_uv[l] <= 100.0f)) return RCT_EINVAL;
+    if (!(step_u >= -16.0f && step_u <= 16.0f && step_v >= -16.0f && step_v <= 16.0f)) return RCT_EINVAL;
+    // the footprint (offsets, 16 warps' starts) must stay inside the image: |du| <= 100 within a width of
+    // 256 leaves room; rows: |dv| <= 100 does not fit 128 rows, so narrower row spans are required
+    float vmin = 0.f, vmax = 0.f;
+    for (int l = 0; l < 32; ++l) {
+        vmin = lane_uv[2 * l + 1] < vmin ? lane_uv[2 * l + 1] : vmin;
+        vmax = lane_uv[2 * l + 1] > vmax ? lane_uv[2 * l + 1] : vmax;
+    }
+    if (vmax - vmin > 40.0f) return RCT_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RCT_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int block = 256, grid = sms * 8;
+    float *img = nullptr;
+    float2 *duv = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rct_status st = RCT_ECUDA;
+    do {
+        if (cudaMalloc(&img, sizeof(float) * (kPatW * kPatH + 4)) != cudaSuccess) { st = RCT_ENOMEM; break; }
+        if (cudaMalloc(&duv, sizeof(float2) * 32) != cudaSuccess) { st = RCT_ENOMEM; break; }
+        if (cudaMemset(img, 0, sizeof(float) * (kPatW * kPatH + 4)) != cudaSuccess) break;
+        // shift the offsets so that the lowest row of the footprint is row 0 of the pattern
+        float2 h[32];
+        for (int l = 0; l < 32; ++l) h[l] = make_float2(lane_uv[2 * l], lane_uv[2 * l + 1] - vmin);
+        if (cudaMemcpy(duv, h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess) break;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) break;
+        float *sink = img + kPatW * kPatH;
+        pattern_probe_kernel<<<grid, block>>>(img, duv, iters, step_u, step_v, sink);
+        if (cudaDeviceSynchronize() != cudaSuccess) break;
+        float best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(e0);
+            pattern_probe_kernel<<<grid, block>>>(img, duv, iters, step_u, step_v, sink);
+            cudaEventRecord(e1);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = ms < best ? ms : best;
+        }
+        if (best >= 1e29f) break;
+        *rate = static_cast<double>(grid) * block * iters / (best * 1e-3);
+        st = RCT_OK;
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (img) cudaFree(img);
+    if (duv) cudaFree(duv);
     return st;
 }
 

@@ -22,6 +22,7 @@ SIGNATURES = {
     "rct_probe_update_stream": (_I, [ctypes.c_size_t, _PD]),
     "rct_probe_l1_bandwidth": (_I, [_I, _PD]),
     "rct_probe_l2_sectors": (_I, [_I, _PD]),
+    "rct_probe_gather_pattern": (_I, [ctypes.POINTER(ctypes.c_float), ctypes.c_float, ctypes.c_float, _I, _PD]),
 }
 
 
@@ -65,4 +66,14 @@ def rct_probe_l1_bandwidth(iters: int = 4096) -> float:
 def rct_probe_l2_sectors(iters: int = 2048) -> float:
     r = ctypes.c_double()
     _check(lib().rct_probe_l2_sectors(iters, ctypes.byref(r)), "rct_probe_l2_sectors")
+    return r.value
+
+
+def rct_probe_gather_pattern(lane_uv, step_u: float, step_v: float, iters: int = 1024) -> float:
+    """Cells per second of the plain-load gather with the warp footprint ``lane_uv`` (32 x 2 pixel offsets)."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(lane_uv, dtype=np.float32).reshape(64))
+    r = ctypes.c_double()
+    _check(lib().rct_probe_gather_pattern(a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), float(step_u),
+                                          float(step_v), iters, ctypes.byref(r)), "rct_probe_gather_pattern")
     return r.value

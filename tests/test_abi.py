@@ -46,7 +46,8 @@ def test_every_declared_symbol_is_exported():
 def test_measurement_library_exports_the_probes():
     from paper_1401_7494_gb300 import probes
     decl = declared_symbols("rct_bench.h")
-    assert decl == {"rct_probe_texture", "rct_probe_update_stream", "rct_probe_l1_bandwidth", "rct_probe_l2_sectors"}
+    assert decl == {"rct_probe_texture", "rct_probe_update_stream", "rct_probe_l1_bandwidth", "rct_probe_l2_sectors",
+                    "rct_probe_gather_pattern"}
     probes.lib()
     assert decl <= exported(pkg_build.BENCH_LIB)
     assert set(probes.SIGNATURES) == decl

@@ -20,6 +20,21 @@ def test_probe_rates_are_plausible(cuda_device):
     assert pair > 1e10
 
 
+def test_gather_pattern_probe_orders_footprints(cuda_device):
+    """The footprint probe: 32 lanes on one cell gather faster than 32 lanes ten pixels apart, which gather
+    faster than lanes spread over rows; its limits are checked."""
+    import numpy as np
+    same = np.zeros((32, 2))
+    row = np.stack([np.arange(32) * 3.0, np.zeros(32)], axis=1)            # 93 px of one row
+    spread = np.stack([(np.arange(32) % 8) * 10.0, (np.arange(32) // 8) * 10.0], axis=1)
+    r_same = probes.rct_probe_gather_pattern(same, 0.0, 10.4, 256)
+    r_row = probes.rct_probe_gather_pattern(row, 0.0, 10.4, 256)
+    r_spread = probes.rct_probe_gather_pattern(spread, 0.0, 10.4, 256)
+    assert r_same > r_row > r_spread > 1e9, (r_same, r_row, r_spread)
+    with pytest.raises(rct.RctError):
+        probes.rct_probe_gather_pattern(np.stack([np.zeros(32), np.arange(32) * 2.0], axis=1), 0.0, 1.0, 64)
+
+
 def test_probe_argument_errors(cuda_device):
     for call in (lambda: probes.rct_probe_l1_bandwidth(1), lambda: probes.rct_probe_l2_sectors(0),
                  lambda: probes.rct_probe_texture(9, rct.RCT_PROJ_F32, 1.0, 1.0, 64),

@@ -117,7 +117,8 @@ def test_concurrent_requests_overlap_on_the_device(setup, cuda_device):
     slots exist (a first batch of the same shapes), the CUDA-event intervals of the chunks' work on their
     requests' streams overlap for a good part of the busy time."""
     protos, host, _ = setup
-    shapes = [(128, "pB", 40), (128, "pB", 40), (96, "pA", 24), (128, "pB", 40), (96, "pA", 24), (128, "pB", 40)]
+    # volumes large enough that a chunk's device work outlasts the host's submission of the next one
+    shapes = [(256, "pB", 40), (256, "pB", 40), (224, "pA", 24), (256, "pB", 40), (224, "pA", 24), (256, "pB", 40)]
     ex = serving.GpuExecutor(protos, host, use_graphs=True)
     sch = serving.Scheduler(ex, 8 << 30, max_active=8)
     warm = sch.run([_req(i, L, p, n, 0.0, "f32") for i, (L, p, n) in enumerate(shapes)])
