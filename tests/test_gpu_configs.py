@@ -162,3 +162,19 @@ def test_sampled_truncating_rule_L512(cuda_device):
     assert_parity(got[~near], ref[~near], f"fp32_L512 truncating rule sampled ({int((~near).sum())} voxels)")
     floor_ref = _sampled_reference(w, host, idx)
     assert np.linalg.norm(floor_ref - ref) / np.linalg.norm(ref) > 1e-6      # the rule changes these sums
+
+
+def test_parity_bar_scales_with_the_detector_width(cuda_device):
+    """The scaled bar's premise, measured: with the field of view and the view count fixed, the FP32 error
+    against the oracle grows with the detector's row length (an FP32 coordinate's rounding grows with its
+    magnitude), and at each width it stays within the bar scaled by W / 1248 and sqrt(496 / views)."""
+    errs = {}
+    for det_w, det_h in [(1248, 960), (4096, 3151)]:
+        w = synth.make_workload(48, n_views=32, det_w=det_w, det_h=det_h, seed=1411)
+        proj = w.projections(device=cuda_device)
+        got = gpu_backproject(w, proj, tuning=tuning_mod.lookup(512, "f32", "soft"))
+        ref = oracle_volume(w, proj.cpu().numpy())
+        del proj
+        errs[det_w] = assert_parity(got, ref, f"{det_w}x{det_h}, 32 views",
+                                    rms_tol=scaled_rms_tol(det_w, w.n_views))[0]
+    assert errs[4096] > 1.5 * errs[1248], errs        # larger coordinates, larger rounding
