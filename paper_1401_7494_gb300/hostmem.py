@@ -16,9 +16,9 @@ buffers, no step slower than the median.
 the huge-page size, advised for transparent huge pages, touched once,
 collapsed into huge pages where the first touch did not get them (a host
 with fragmented memory), and registered with ``cudaHostRegister``;
-``huge_fraction`` reports how much of a buffer huge pages back.  The returned tensor owns the buffer:
-it is unregistered and unmapped when the tensor and every view of it are
-gone.  Where transparent huge pages are switched off the buffer is still
+``huge_fraction`` reports how much of a buffer huge pages back.  The
+returned tensor owns the buffer: it is unregistered and unmapped when the
+tensor and every view of it are gone.  Where transparent huge pages are switched off the buffer is still
 aligned, locked and registered, in base pages.
 """
 from __future__ import annotations
@@ -27,8 +27,11 @@ import ctypes
 import ctypes.util
 from pathlib import Path
 
+_PROT_NONE = 0
 _PROT_RW = 0x1 | 0x2
 _MAP_PRIVATE_ANON = 0x02 | 0x20
+_MAP_FIXED = 0x10
+_MAP_NORESERVE = 0x4000
 _MADV_HUGEPAGE = 14
 _MADV_COLLAPSE = 25       # Linux 6.1+: make the range huge pages now (compacting memory if it must)
 _THP = Path("/sys/kernel/mm/transparent_hugepage")
@@ -63,8 +66,49 @@ def huge_pages_enabled() -> bool:
         return False
 
 
-def pinned_empty(shape, dtype):
-    """A page-locked, huge-page-backed host tensor of ``shape`` and ``dtype`` (contents zero)."""
+def _vma_table():
+    """(start, end, AnonHugePages bytes) of every mapping of this process, from /proc/self/smaps."""
+    out = []
+    try:
+        lines = Path("/proc/self/smaps").read_text().splitlines()
+    except OSError:
+        return out
+    cur = None
+    for line in lines:
+        parts = line.split()
+        if not parts:
+            continue
+        if "-" in parts[0] and ":" not in parts[0]:
+            lo, hi = (int(x, 16) for x in parts[0].split("-"))
+            cur = [lo, hi, 0]
+            out.append(cur)
+        elif cur is not None and parts[0] == "AnonHugePages:":
+            cur[2] = int(parts[1]) * 1024
+    return out
+
+
+def _huge_bytes(lo: int, hi: int) -> int:
+    """Bytes of [lo, hi) that transparent huge pages back (mappings wholly inside the range)."""
+    return sum(h for a, b, h in _vma_table() if lo <= a and b <= hi)
+
+
+def _map_chunk(libc, addr: int, n: int) -> None:
+    got = libc.mmap(addr, n, _PROT_RW, _MAP_PRIVATE_ANON | _MAP_FIXED, -1, 0)
+    if got != addr:
+        raise MemoryError(f"mmap of {n} bytes at a fixed address failed (errno {ctypes.get_errno()})")
+    libc.madvise(addr, n, _MADV_HUGEPAGE)
+    ctypes.memset(addr, 0, n)                      # touch every page before it is locked
+    libc.madvise(addr, n, _MADV_COLLAPSE)          # best effort: fails harmlessly where unsupported
+
+
+def pinned_empty(shape, dtype, tries: int = 3):
+    """A page-locked, huge-page-backed host tensor of ``shape`` and ``dtype`` (contents zero).
+
+    The buffer is mapped one huge page at a time inside an aligned reserved range (at most 64 of them; more,
+    smaller huge pages are mapped in one go); a huge page that comes back in base pages (a host whose free
+    memory is fragmented) is mapped again, up to ``tries`` times, each attempt asking the kernel to compact
+    memory for it.  What still fails stays in base pages: the buffer
+    works, more slowly on such hosts (``huge_fraction`` tells)."""
     import torch
     libc = _c()
     n = 1
@@ -77,12 +121,11 @@ def pinned_empty(shape, dtype):
     huge = huge_pages_enabled() and nbytes >= hp // 4
     size = max(hp, -(-nbytes // hp) * hp) if huge else max(1, nbytes)
     raw_size = size + hp
-    raw = libc.mmap(None, raw_size, _PROT_RW, _MAP_PRIVATE_ANON, -1, 0)
+    raw = libc.mmap(None, raw_size, _PROT_NONE if huge else _PROT_RW,
+                    _MAP_PRIVATE_ANON | (_MAP_NORESERVE if huge else 0), -1, 0)
     if raw in (None, ctypes.c_void_p(-1).value):
         raise MemoryError(f"mmap of {raw_size} bytes failed (errno {ctypes.get_errno()})")
     start = -(-raw // hp) * hp
-    if huge:
-        libc.madvise(start, size, _MADV_HUGEPAGE)
     cudart = torch.cuda.cudart()
 
     class _Mapping(ctypes.c_char * size):
@@ -96,11 +139,19 @@ def pinned_empty(shape, dtype):
             finally:
                 libc.munmap(raw, raw_size)
 
+    if huge and size // hp > 64:
+        _map_chunk(libc, start, size)             # small huge pages (2 MiB): one mapping, one collapse
+    elif huge:
+        for at in range(start, start + size, hp):
+            for _ in range(max(1, tries)):
+                before = _huge_bytes(start, start + size)
+                _map_chunk(libc, at, hp)
+                if _huge_bytes(start, start + size) - before >= hp:
+                    break
     mapping = _Mapping.from_address(start)
     t = torch.frombuffer(mapping, dtype=torch.uint8)
-    t.zero_()                                     # touch every page before it is locked
-    if huge:
-        libc.madvise(start, size, _MADV_COLLAPSE)  # best effort: fails harmlessly where unsupported
+    if not huge:
+        t.zero_()                                 # touch every page before it is locked
     err = cudart.cudaHostRegister(start, size, 0)
     if int(err) != 0:
         raise RuntimeError(f"cudaHostRegister of {size} bytes failed: {err}")
@@ -109,24 +160,11 @@ def pinned_empty(shape, dtype):
 
 
 def huge_fraction(t) -> float:
-    """Fraction of the memory mapping that holds tensor ``t`` which transparent huge pages back (from
-    /proc/self/smaps; 0.0 where the mapping is not found)."""
+    """Fraction of the bytes of the buffer holding tensor ``t`` (from its start to the end of its mapping
+    range) that transparent huge pages back, from /proc/self/smaps (0.0 where nothing is found)."""
     addr = t.data_ptr()
-    try:
-        lines = Path("/proc/self/smaps").read_text().splitlines()
-    except OSError:
-        return 0.0
-    inside = False
-    size = huge = 0
-    for line in lines:
-        head = line.split()[0] if line.split() else ""
-        if "-" in head and ":" not in head:
-            lo, hi = (int(x, 16) for x in head.split("-"))
-            inside = lo <= addr < hi
-            continue
-        if inside and line.startswith("Size:"):
-            size = int(line.split()[1])
-        elif inside and line.startswith("AnonHugePages:"):
-            huge = int(line.split()[1])
-            break
-    return huge / size if size else 0.0
+    nbytes = t.numel() * t.element_size()
+    hp = huge_page_bytes()
+    hi = addr + max(hp, -(-nbytes // hp) * hp)
+    total = sum(min(b, hi) - max(a, addr) for a, b, _ in _vma_table() if a < hi and b > addr)
+    return min(1.0, _huge_bytes(addr, hi) / total) if total else 0.0

@@ -71,3 +71,26 @@ def test_numpy_interop(fake):
     a = t.numpy()
     a[:] = np.arange(48, dtype=np.float32).reshape(6, 8)
     assert float(t[5, 7]) == 47.0
+
+
+def test_a_chunk_left_in_base_pages_is_mapped_again(fake, monkeypatch):
+    """A huge page that comes back in base pages is mapped again (up to `tries` times); the others once."""
+    monkeypatch.setattr(hostmem, "huge_page_bytes", lambda: 1 << 20)
+    monkeypatch.setattr(hostmem, "huge_pages_enabled", lambda: True)
+    calls = []
+    real_map = hostmem._map_chunk
+    got = {"huge": 0}
+
+    def map_chunk(libc, addr, n):
+        real_map(libc, addr, n)
+        calls.append(addr)
+        # the second chunk gets its huge page only on the third attempt
+        idx = sorted(set(calls)).index(addr)
+        if idx != 1 or calls.count(addr) >= 3:
+            got["huge"] += n
+    monkeypatch.setattr(hostmem, "_map_chunk", map_chunk)
+    monkeypatch.setattr(hostmem, "_huge_bytes", lambda lo, hi: got["huge"])
+    t = hostmem.pinned_empty((3, 1 << 18), torch.float32, tries=3)      # 3 MiB: three chunks
+    base = t.data_ptr()
+    assert calls == [base, base + (1 << 20), base + (1 << 20), base + (1 << 20), base + (2 << 20)]
+    assert torch.count_nonzero(t) == 0
