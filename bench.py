@@ -60,13 +60,17 @@ def traffic_records() -> list:
     return out
 
 
-def recorded_traffic(dtype: str, tun: dict):
-    """(bytes per accumulating launch, summary file) recorded for this kernel source and tuning, else (None, None)."""
+def recorded_traffic(dtype: str, tun: dict, L: int):
+    """The traffic record (ncu counters of one accumulating launch: ``bytes`` = DRAM read + write, optionally
+    ``lsu_wavefronts`` and the launch's voxel ``updates``) for this volume size, storage type, tuning and kernel
+    source, with its summary file under ``source``; None where no capture matches."""
     src = kernel_source_hash()
+    plain = lambda t: {k: v for k, v in t.items() if not (k == "view_split" and v == 1)}   # 1 = no split
     for rec in traffic_records():
-        if rec.get("dtype") == dtype and rec.get("tuning") == tun and rec.get("kernel_source") == src:
-            return int(rec["bytes"]), rec["source"]
-    return None, None
+        if (rec.get("dtype") == dtype and plain(rec.get("tuning", {})) == plain(tun)
+                and rec.get("kernel_source") == src and rec.get("L") == L):
+            return rec
+    return None
 
 
 def parse_args():
@@ -558,7 +562,8 @@ def run_ours(args, dist: Dist) -> dict | None:
     bytes_per_launch = bytes_per_step / passes_per_step
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved_gbs = bytes_per_launch / avg_kernel_s / 1e9
-    traffic, traffic_src = (recorded_traffic(args.dtype, tun) if w.L == 512 and w.n_views == 496 else (None, None))
+    rec = recorded_traffic(args.dtype, tun, w.L) if w.n_views == 496 else None
+    traffic, traffic_src = (int(rec["bytes"]), rec["source"]) if rec else (None, None)
     # texture route: one tld4 gather per voxel update against the gather rate the probe measures for the
     # storage type of the step (the texture unit, not the load/store data path, fetches these cells)
     live = live_warp_fraction(w, tun)
@@ -600,6 +605,24 @@ def run_ours(args, dist: Dist) -> dict | None:
                 "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                         "frac": round(achieved_gbs / hbm_peak, 4), "algorithmic_bytes_per_launch": int(bytes_per_launch),
                         "peak_source": "measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks else "fallback"}}
+    if rec and rec.get("lsu_wavefronts") and rec.get("updates"):
+        # The unit that binds the load routes, counted: L1 data-pipe wavefronts (one per clock per SM at most).
+        # ncu counts them for one launch of this kernel source and tuning; they scale with the launch's voxel
+        # updates (the clip test keeps the same share of every view), so the average launch of the step
+        # issues the recorded count x its updates / the recorded launch's updates, in the measured launch time.
+        wf = rec["lsu_wavefronts"] * upd_per_launch / rec["updates"]
+        wf_rate = wf / avg_kernel_s / 1e9
+        wf_peak = sms * sm_mhz * 1e6 / 1e9
+        roofline["l1_data_pipe"] = {
+            "achieved": round(wf_rate, 1), "peak": round(wf_peak, 1), "unit": "Gwavefront/s",
+            "frac": round(wf_rate / wf_peak, 4), "wavefronts_per_launch": int(wf),
+            "wavefronts_per_update": round(wf / upd_per_launch, 3),
+            "what": "L1 data-pipe wavefronts of the gather's loads (the count of an ncu capture, scaled to the "
+                    "average launch) over the launch time measured in this run",
+            "peak_source": f"derived: 1 wavefront/clk/SM x {sms} SMs x {sm_mhz:.0f} MHz (median SM clock sampled "
+                           "during the timed region)",
+            "count_source": f"profiles/{rec['source']}: l1tex__data_pipe_lsu_wavefronts.sum of a launch of "
+                            f"{rec['updates']} voxel updates"}
     if route == "ldg" and args.dtype == "f32":
         # Plain loads of four 4-byte taps: where lanes land far apart (L=128: 10 px) the L1 data pipe's
         # wavefronts, not its bytes, bind.  The ceiling of this access pattern is measured by replaying the

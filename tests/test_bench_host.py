@@ -55,28 +55,40 @@ def test_live_warp_fraction_matches_exhaustive_count():
 
 
 def test_traffic_records(tmp_path, monkeypatch):
-    """Traffic per launch comes from a record in a profile summary, and counts only for the same storage
-    type, tuning and kernel source."""
+    """Traffic per launch comes from a record in a profile summary, and counts only for the same volume size,
+    storage type, tuning and kernel source."""
     for rec in bench.traffic_records():                     # every committed record is well formed
         assert rec["dtype"] in ("f32", "f16", "bf16")
-        assert set(rec["tuning"]) == {"block_x", "block_y", "gather", "tex_zrun", "views_per_pass", "xvec", "zrun"}
-        assert 1e9 < rec["bytes"] < 2e9                       # one accumulating pass at 512^3: ~1.1-1.3 GB
+        assert set(rec["tuning"]) - {"view_split"} == {"block_x", "block_y", "gather", "tex_zrun",
+                                                        "views_per_pass", "xvec", "zrun"}
+        assert rec["L"] in (128, 256, 512, 1024)
+        # one accumulating pass: the volume read and written plus the pass's views (a capture can end with
+        # some of the volume's writes still in L2)
+        assert 0.9 * 2 * 4 * rec["L"] ** 3 < rec["bytes"] < 2 * 4 * rec["L"] ** 3 + 40 * 4 * 1248 * 960 * 1.2
+        assert rec["updates"] == rec["L"] ** 3 * rec["tuning"]["views_per_pass"]
+        if "lsu_wavefronts" in rec:                          # 1-40 wavefronts per warp update
+            assert rec["updates"] / 32 < rec["lsu_wavefronts"] < 40 * rec["updates"] / 32
         assert len(rec["kernel_source"]) == 16
     tun = {"block_x": 8, "block_y": 16, "gather": 5, "tex_zrun": 0, "views_per_pass": 24, "xvec": 1, "zrun": 8}
     prof = tmp_path / "profiles"
     prof.mkdir()
-    rec = {"dtype": "f32", "tuning": tun, "kernel_source": bench.kernel_source_hash(), "bytes": 1269302272}
+    rec = {"dtype": "f32", "L": 512, "tuning": tun, "kernel_source": bench.kernel_source_hash(),
+           "bytes": 1269302272, "updates": 512 ** 3 * 24}
     (prof / "x.md").write_text("# summary\n\ntraffic-record: " + json.dumps(rec) + "\n")
     real_root = bench.ROOT
     monkeypatch.setattr(bench, "ROOT", tmp_path)
     for rel in bench.KERNEL_SOURCES:                        # the same kernel sources under the fake root
         (tmp_path / rel).parent.mkdir(parents=True, exist_ok=True)
         (tmp_path / rel).write_bytes((real_root / rel).read_bytes())
-    assert bench.recorded_traffic("f32", tun) == (1269302272, "x.md")
-    assert bench.recorded_traffic("f16", tun) == (None, None)
-    assert bench.recorded_traffic("f32", dict(tun, zrun=16)) == (None, None)
+    got = bench.recorded_traffic("f32", tun, 512)
+    assert got["bytes"] == 1269302272 and got["source"] == "x.md"
+    assert bench.recorded_traffic("f32", dict(tun, view_split=1), 512)["bytes"] == 1269302272
+    assert bench.recorded_traffic("f32", dict(tun, view_split=2), 512) is None
+    assert bench.recorded_traffic("f32", tun, 1024) is None
+    assert bench.recorded_traffic("f16", tun, 512) is None
+    assert bench.recorded_traffic("f32", dict(tun, zrun=16), 512) is None
     (tmp_path / bench.KERNEL_SOURCES[0]).write_text("// changed kernel\n")
-    assert bench.recorded_traffic("f32", tun) == (None, None)
+    assert bench.recorded_traffic("f32", tun, 512) is None
 
 
 def _json_lines(text):
