@@ -468,6 +468,24 @@ def k_sweep(dev, stream, peaks: dict) -> dict:
                     "each view read once"}
 
 
+VM_EVENTS = ("pgmigrate_success", "compact_migrate_scanned", "compact_free_scanned", "compact_isolated",
+             "compact_stall", "compact_daemon_wake", "thp_collapse_alloc", "thp_fault_alloc", "thp_fault_fallback")
+
+
+def vm_events() -> dict:
+    """The host's page-migration and compaction event counters (/proc/vmstat; empty where unreadable)."""
+    try:
+        text = Path("/proc/vmstat").read_text()
+    except OSError:
+        return {}
+    out = {}
+    for line in text.splitlines():
+        k, _, v = line.partition(" ")
+        if k in VM_EVENTS:
+            out[k] = int(v)
+    return out
+
+
 def run_ours(args, dist: Dist) -> dict | None:
     import torch
     import synth
@@ -490,6 +508,15 @@ def run_ours(args, dist: Dist) -> dict | None:
         data = torch.empty(proj.shape, dtype={"f16": torch.float16, "bf16": torch.bfloat16}[args.dtype], device=dev)
         rct.rct_convert_projections(proj, data, proj.numel(), codes[args.dtype], stream)
     torch.cuda.synchronize()
+    host_bufs = None
+    if not args.no_e2e:
+        # The end-to-end leg's page-locked host buffers, backed by aligned huge pages (hostmem: copies run at the
+        # link rate without the stalls that base-page pinned buffers show on hosts whose memory has been
+        # churned).  They are allocated here, before the timed step, so that any memory compaction the huge-page
+        # requests set off on the host has the step's duration to settle before the end-to-end copies are timed.
+        from paper_1401_7494_gb300 import hostmem
+        host_bufs = (hostmem.pinned_empty(data.shape, data.dtype), hostmem.pinned_empty((w.L,) * 3, torch.float32))
+        host_bufs[0].copy_(data)
     tun = tuning.lookup(w.L, args.dtype, "soft")
     if args.tuning:
         tun = dict(tun, **json.loads(args.tuning))
@@ -661,12 +688,9 @@ def run_ours(args, dist: Dist) -> dict | None:
 
     # --- end to end through the public API with host buffers
     if not args.no_e2e:
-        # page-locked host buffers backed by aligned huge pages (hostmem): the copies run at the link rate
-        # without the stalls that base-page pinned buffers show on hosts whose memory has been churned
         from paper_1401_7494_gb300 import hostmem
-        pinned = hostmem.pinned_empty(data.shape, data.dtype)
-        pinned.copy_(data)
-        vol_host = hostmem.pinned_empty((w.L,) * 3, torch.float32)
+        pinned, vol_host = host_bufs
+        host_bufs = None
         for _ in range(max(1, args.warmup)):
             bp.reset(stream)
             bp.backproject_host_read(pinned, vol_host, 0, w.n_views, stream)
@@ -688,6 +712,7 @@ def run_ours(args, dist: Dist) -> dict | None:
         copy_before = plain_copy_gbs()
         e_steps = max(2, args.steps)
         dist.barrier()
+        vm0 = vm_events()
         t0 = time.perf_counter()
         marks = [torch.cuda.Event(enable_timing=True) for _ in range(e_steps + 1)]
         marks[0].record(stream)
@@ -700,6 +725,7 @@ def run_ours(args, dist: Dist) -> dict | None:
             marks[i + 1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        vm1 = vm_events()
         e_ms = max(marks[0].elapsed_time(marks[-1]), wall * 1e3)
         e_ms = dist.max(e_ms)
         in_order = [marks[i].elapsed_time(marks[i + 1]) for i in range(e_steps)]
@@ -744,6 +770,8 @@ def run_ours(args, dist: Dist) -> dict | None:
                                   "max": round(per_step[-1], 3), "in_order": [round(t, 2) for t in in_order]},
                       "host_enqueue_ms": [round(t, 2) for t in enqueue],
                       "plain_copy_gbs": {"before": copy_before, "after": copy_after},
+                      # the host's page migration and compaction during the timed region (system-wide counters)
+                      "host_vm_events": {k: vm1[k] - vm0[k] for k in vm1 if k in vm0} if vm0 and vm1 else None,
                       "graph_replay": {
                              "value": round(dist.sum(float(w.updates * e_steps)) / (g_ms / 1e3) / 1e9, 2),
                              "unit": UNIT, "ms_per_step": round(g_ms / e_steps, 3),
