@@ -45,6 +45,17 @@ def _valid(L: int, t: dict, dtype: str = "f32") -> bool:
     return L % t["xvec"] == 0 and bx * by <= 512 and (bx * by) % 32 == 0
 
 
+def search_params(interp: str, frame: str) -> list:
+    """The tuning fields the descent varies.  Texture filtering has one gather; the view split runs only with
+    software interpolation in the global frame (the library rejects it elsewhere)."""
+    params = ["gather", "views_per_pass", "zrun", "xvec", "block", "view_split"]
+    if interp == "tex":
+        params.remove("gather")
+    if interp == "tex" or frame == "block":
+        params.remove("view_split")
+    return params
+
+
 def time_candidate(bp, data, n_views: int, stream, reps: int = 3) -> float:
     """Seconds per backprojection of n_views views (best of reps after one warm-up)."""
     import torch
@@ -121,10 +132,7 @@ def autotune(w, data, dtype: str = "f32", interp: str = "soft", n_views: int | N
             log(f"  {t} -> {g:.1f} GUPS")
             return g
 
-        params = ["gather", "views_per_pass", "zrun", "xvec", "block", "view_split"]
-        if interp == "tex":
-            params.remove("gather")
-            params.remove("view_split")
+        params = search_params(interp, frame)
         best_all, cur_all = -1.0, None
         for cur in starts:
             best = measure(cur)

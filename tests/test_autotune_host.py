@@ -50,3 +50,13 @@ def test_tuning_cache_round_trip_and_fallbacks(tmp_path):
     assert tuning.lookup(512, "f32", "soft", gpu="Other GPU", path=path) == tuning.DEFAULT
     # the default drops the x-vector for a volume it does not divide
     assert tuning.lookup(37, "f32", "soft", gpu=gpu, path=path)["xvec"] == 1
+
+
+def test_search_leaves_out_what_the_library_rejects():
+    """The view split is searched only with software interpolation in the global frame (the library returns
+    RCT_ENOTSUP for it with block frames or texture filtering, which once ended a block-frame search)."""
+    assert "view_split" in autotune.search_params("soft", "global")
+    assert "view_split" not in autotune.search_params("soft", "block")
+    assert "view_split" not in autotune.search_params("tex", "global")
+    assert "gather" not in autotune.search_params("tex", "global")
+    assert autotune.search_params("soft", "block") == ["gather", "views_per_pass", "zrun", "xvec", "block"]
