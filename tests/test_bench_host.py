@@ -63,8 +63,10 @@ def test_traffic_records(tmp_path, monkeypatch):
                                                         "views_per_pass", "xvec", "zrun"}
         assert rec["L"] in (128, 256, 512, 1024)
         # one accumulating pass: the volume read and written plus the pass's views (a capture can end with
-        # some of the volume's writes still in L2)
-        assert 0.9 * 2 * 4 * rec["L"] ** 3 < rec["bytes"] < 2 * 4 * rec["L"] ** 3 + 40 * 4 * 1248 * 960 * 1.2
+        # some of the volume's writes still in L2; a register-capped kernel's spills can add up to its
+        # algorithmic bytes again)
+        algo = 2 * 4 * rec["L"] ** 3 + rec["tuning"]["views_per_pass"] * 4 * 1248 * 960
+        assert 0.85 * algo < rec["bytes"] < 2.0 * algo
         assert rec["updates"] == rec["L"] ** 3 * rec["tuning"]["views_per_pass"]
         if "lsu_wavefronts" in rec:                          # 1-40 wavefronts per warp update
             assert rec["updates"] / 32 < rec["lsu_wavefronts"] < 40 * rec["updates"] / 32
