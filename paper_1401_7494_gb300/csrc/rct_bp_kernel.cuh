@@ -536,14 +536,18 @@ __global__ void __launch_bounds__(512) bp_kernel(const __grid_constant__ BpParam
 }
 
 // Register caps (measured): the block-frame kernels keep the frame's rows and shift in per-thread
-// registers through the z-run, and the z-runs of 16 keep 16 partial sums; capped at
-// RCT_CAPPED_MAXREG registers both keep more warps resident and run faster, while the global-frame
-// kernels with shorter z-runs run slower under any cap.
+// registers through the z-run, and the z-runs of 16 keep 16 partial sums; capped, both keep more warps
+// resident and run faster, while the global-frame kernels with shorter z-runs run slower under any cap.
+// Swept at L=512 x 496 (pairs, K=32, z-run 16): global frame 40 / 48 / 56 / 64 registers gave 1224 / 1314 /
+// 1304 / 1248 GUPS, block frame 1113 / 1257 / 1282 / 1236.
 #ifndef RCT_CAPPED_MAXREG
 #define RCT_CAPPED_MAXREG 48
 #endif
+#ifndef RCT_FRAME_MAXREG
+#define RCT_FRAME_MAXREG 56
+#endif
 template <int DT, int XV, int R, int ROUTE>
-__global__ void __maxnreg__(RCT_CAPPED_MAXREG) bp_kernel_frame(const __grid_constant__ BpParams p) {
+__global__ void __maxnreg__(RCT_FRAME_MAXREG) bp_kernel_frame(const __grid_constant__ BpParams p) {
     bp_body<G_SOFT, DT, XV, R, ROUTE, true, false>(p);
 }
 

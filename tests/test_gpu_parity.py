@@ -569,3 +569,19 @@ def test_view_split_needs_the_global_frame(small_cases):
         assert e.value.status == rct.RCT_ENOTSUP
         with pytest.raises(rct.RctError):
             bp.set_tuning(view_split=3)
+
+
+@pytest.mark.parametrize("gather", [rct.RCT_GATHER_PAIR, rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG])
+def test_lane_map_does_not_change_bits(small_cases, gather):
+    """Blocks 8 threads wide hand each half warp a 4 x 4 patch of voxel columns (fewer cache lines per 8-byte
+    load); other widths keep the row order.  Which lane computes a voxel must not change its sum: in the global
+    frame the volumes of 8 x 16 and 8 x 8 blocks (lane map) equal those of 16 x 8 and 32 x 4 blocks bit for bit,
+    with ragged tails in x, y and z (L = 40)."""
+    w, proj, host = small_cases["L40"]
+    base = dict(gather=gather, views_per_pass=11, zrun=4, xvec=1)
+    vols = {(bx, by): gpu_backproject(w, proj, tuning=dict(base, block_x=bx, block_y=by))
+            for bx, by in [(8, 16), (8, 8), (16, 8), (32, 4)]}
+    ref = vols[(16, 8)]
+    for shape, v in vols.items():
+        assert np.array_equal(v, ref), f"block {shape} differs from 16 x 8"
+    assert_parity(ref, oracle_volume(w, host), f"lane map, gather {gather}")
