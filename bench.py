@@ -468,6 +468,11 @@ def k_sweep(dev, stream, peaks: dict) -> dict:
                     "each view read once"}
 
 
+# Host-to-device plain-copy rate (GB/s) taken as a ready host link before the end-to-end timed region: half
+# of the 210 GB/s these hosts sustain from page-locked memory; the wait for it is bounded.
+LINK_READY_GBS = 100.0
+LINK_WAIT_S = 60.0
+
 VM_EVENTS = ("pgmigrate_success", "compact_migrate_scanned", "compact_free_scanned", "compact_isolated",
              "compact_stall", "compact_daemon_wake", "thp_collapse_alloc", "thp_fault_alloc", "thp_fault_fallback")
 
@@ -710,6 +715,16 @@ def run_ours(args, dist: Dist) -> dict | None:
                     "d2h": round(vol_host.numel() * 4 / (c1.elapsed_time(c2) / 1e3) / 1e9, 1)}
 
         copy_before = plain_copy_gbs()
+        # Some hosts slow this process's host-to-device reads for tens of seconds at a time (plain copies at
+        # 9-55 GB/s instead of the link's 210, with no page migration or compaction on the host; the cause is
+        # outside this process).  The timed region waits, up to LINK_WAIT_S, for a plain copy at half the
+        # link's rate; the samples and the wait are reported beside the result.
+        link_wait = {"seconds": 0.0, "h2d_samples": []}
+        while copy_before["h2d"] < LINK_READY_GBS and link_wait["seconds"] < LINK_WAIT_S:
+            time.sleep(5.0)
+            link_wait["seconds"] += 5.0
+            copy_before = plain_copy_gbs()
+            link_wait["h2d_samples"].append(copy_before["h2d"])
         e_steps = max(2, args.steps)
         dist.barrier()
         vm0 = vm_events()
@@ -770,6 +785,7 @@ def run_ours(args, dist: Dist) -> dict | None:
                                   "max": round(per_step[-1], 3), "in_order": [round(t, 2) for t in in_order]},
                       "host_enqueue_ms": [round(t, 2) for t in enqueue],
                       "plain_copy_gbs": {"before": copy_before, "after": copy_after},
+                      "host_link_wait": link_wait,
                       # the host's page migration and compaction during the timed region (system-wide counters)
                       "host_vm_events": {k: vm1[k] - vm0[k] for k in vm1 if k in vm0} if vm0 and vm1 else None,
                       "graph_replay": {
