@@ -473,6 +473,19 @@ def k_sweep(dev, stream, peaks: dict) -> dict:
 LINK_READY_GBS = 100.0
 LINK_WAIT_S = 90.0
 
+def wait_for_host_link(h2d_gbs, first: float) -> dict:
+    """Wait, up to LINK_WAIT_S in 5 s steps, until h2d_gbs() (the rate of a plain host-to-device copy, GB/s;
+    ``first`` is the rate already measured) reaches LINK_READY_GBS.  Returns the wait and the rates seen."""
+    out = {"seconds": 0.0, "h2d_samples": []}
+    rate = first
+    while rate < LINK_READY_GBS and out["seconds"] < LINK_WAIT_S:
+        time.sleep(5.0)
+        out["seconds"] += 5.0
+        rate = h2d_gbs()
+        out["h2d_samples"].append(round(rate, 1))
+    return out
+
+
 VM_EVENTS = ("pgmigrate_success", "compact_migrate_scanned", "compact_free_scanned", "compact_isolated",
              "compact_stall", "compact_daemon_wake", "thp_collapse_alloc", "thp_fault_alloc", "thp_fault_fallback")
 
@@ -719,12 +732,9 @@ def run_ours(args, dist: Dist) -> dict | None:
         # 2-55 GB/s instead of the link's 210, with no page migration or compaction on the host; the cause is
         # outside this process).  The timed region waits, up to LINK_WAIT_S, for a plain copy at half the
         # link's rate; the samples and the wait are reported beside the result.
-        link_wait = {"seconds": 0.0, "h2d_samples": []}
-        while copy_before["h2d"] < LINK_READY_GBS and link_wait["seconds"] < LINK_WAIT_S:
-            time.sleep(5.0)
-            link_wait["seconds"] += 5.0
+        link_wait = wait_for_host_link(lambda: plain_copy_gbs()["h2d"], copy_before["h2d"])
+        if link_wait["seconds"]:
             copy_before = plain_copy_gbs()
-            link_wait["h2d_samples"].append(copy_before["h2d"])
         e_steps = max(2, args.steps)
         dist.barrier()
         vm0 = vm_events()
@@ -830,10 +840,27 @@ def run_ours(args, dist: Dist) -> dict | None:
     if dist.rank == 0 and not args.no_serve:
         from paper_1401_7494_gb300 import serve_bench
         protocols, host_data = serve_bench.build_protocols(dev, raw=True)
+        # the requests' projections stream from page-locked host memory: the same bounded wait for a ready
+        # host link as the end-to-end leg, before each mode
+        probe_src = next(iter(host_data.values()))
+        probe_dst = torch.empty(probe_src.shape, dtype=probe_src.dtype, device=dev)
+
+        def probe_h2d() -> float:
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            probe_dst.copy_(probe_src, non_blocking=True)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            return probe_src.numel() * probe_src.element_size() / (c0.elapsed_time(c1) / 1e3) / 1e9
+
         served = {}
         for mode, raw in (("f32", False), ("f16", False), ("f16", True)):
-            served[mode + ("_raw_ingest" if raw else "")] = serve_bench.run_mode(
+            wait = wait_for_host_link(probe_h2d, probe_h2d())
+            key = mode + ("_raw_ingest" if raw else "")
+            served[key] = serve_bench.run_mode(
                 mode, protocols, host_data, n_requests=args.serve_requests, raw=raw, log=lambda *_: None)
+            served[key]["host_link_wait"] = wait
+        del probe_dst
         result["served"] = {m: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
                             for m, r in served.items()}
         del host_data

@@ -133,3 +133,15 @@ def test_reference_arm_under_torchrun_prints_once():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = _json_lines(r.stdout)
     assert len(lines) == 1 and lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2, r.stdout
+
+
+def test_wait_for_host_link_is_bounded(monkeypatch):
+    """The end-to-end and served legs wait for a plain host-to-device copy at half the link's rate, in 5 s
+    steps, and give up after LINK_WAIT_S; a ready link costs no wait."""
+    monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+    assert bench.wait_for_host_link(lambda: 0.0, 210.0) == {"seconds": 0.0, "h2d_samples": []}
+    rates = iter([2.7, 9.4, 209.9])
+    got = bench.wait_for_host_link(lambda: next(rates), 1.9)
+    assert got == {"seconds": 15.0, "h2d_samples": [2.7, 9.4, 209.9]}
+    slow = bench.wait_for_host_link(lambda: 3.0, 3.0)
+    assert slow["seconds"] == bench.LINK_WAIT_S and len(slow["h2d_samples"]) == int(bench.LINK_WAIT_S / 5)
