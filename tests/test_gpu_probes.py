@@ -21,8 +21,10 @@ def test_probe_rates_are_plausible(cuda_device):
 
 
 def test_gather_pattern_probe_orders_footprints(cuda_device):
-    """The footprint probe: 32 lanes on one cell gather faster than 32 lanes ten pixels apart, which gather
-    faster than lanes spread over rows; its limits are checked."""
+    """The footprint probe: lanes on one cell or along one row (a few cache lines) gather much faster than
+    lanes spread over four rows ten pixels apart; the first two both run at the probe's instruction rate
+    (measured 0.999e12 and 1.012e12 cells/s on one box), so they are compared within noise only.  Its limits
+    are checked."""
     import numpy as np
     same = np.zeros((32, 2))
     row = np.stack([np.arange(32) * 3.0, np.zeros(32)], axis=1)            # 93 px of one row
@@ -30,7 +32,7 @@ def test_gather_pattern_probe_orders_footprints(cuda_device):
     r_same = probes.rct_probe_gather_pattern(same, 0.0, 10.4, 256)
     r_row = probes.rct_probe_gather_pattern(row, 0.0, 10.4, 256)
     r_spread = probes.rct_probe_gather_pattern(spread, 0.0, 10.4, 256)
-    assert r_same > r_row > r_spread > 1e9, (r_same, r_row, r_spread)
+    assert r_same > 0.9 * r_row and min(r_same, r_row) > 1.3 * r_spread and r_spread > 1e9, (r_same, r_row, r_spread)
     with pytest.raises(rct.RctError):
         probes.rct_probe_gather_pattern(np.stack([np.zeros(32), np.arange(32) * 2.0], axis=1), 0.0, 1.0, 64)
 
