@@ -94,3 +94,28 @@ def test_a_chunk_left_in_base_pages_is_mapped_again(fake, monkeypatch):
     base = t.data_ptr()
     assert calls == [base, base + (1 << 20), base + (1 << 20), base + (1 << 20), base + (2 << 20)]
     assert torch.count_nonzero(t) == 0
+
+
+def _locked_bytes(addr: int) -> int:
+    """The Locked: bytes of the mapping of this process that contains addr (/proc/self/smaps)."""
+    cur = None
+    for line in open("/proc/self/smaps").read().splitlines():
+        parts = line.split()
+        if parts and "-" in parts[0] and ":" not in parts[0]:
+            lo, hi = (int(x, 16) for x in parts[0].split("-"))
+            cur = lo <= addr < hi
+        elif cur and parts and parts[0] == "Locked:":
+            return int(parts[1]) * 1024
+    return 0
+
+
+def test_buffer_is_locked_where_the_limit_allows(fake):
+    """Buffers are mlock-ed before registration (out of the reclaim scans); a lock limit smaller than the
+    buffer leaves it unlocked but usable."""
+    import resource
+    soft, _ = resource.getrlimit(resource.RLIMIT_MEMLOCK)
+    t = hostmem.pinned_empty((1024,), torch.float32)
+    if soft == resource.RLIM_INFINITY or soft >= 64 * 1024:
+        assert _locked_bytes(t.data_ptr()) >= t.numel() * t.element_size()
+    t[:] = 1.0
+    assert float(t.sum()) == 1024.0
