@@ -531,9 +531,14 @@ def run_ours(args, dist: Dist) -> dict | None:
         # The end-to-end leg's page-locked host buffers, backed by aligned huge pages (hostmem: copies run at the
         # link rate without the stalls that base-page pinned buffers show on hosts whose memory has been
         # churned).  They are allocated here, before the timed step, so that any memory compaction the huge-page
-        # requests set off on the host has the step's duration to settle before the end-to-end copies are timed.
+        # requests set off on the host has the step's duration to settle before the end-to-end copies are timed;
+        # they are locked and registered only then (hostmem.finish), after one more try for huge pages where
+        # the first attempt got base pages.
         from paper_1401_7494_gb300 import hostmem
-        host_bufs = (hostmem.pinned_empty(data.shape, data.dtype), hostmem.pinned_empty((w.L,) * 3, torch.float32))
+        host_bufs = (hostmem.pinned_empty(data.shape, data.dtype, register=False),
+                     hostmem.pinned_empty((w.L,) * 3, torch.float32, register=False))
+        huge_at_allocation = {"projections": round(hostmem.huge_fraction(host_bufs[0]), 3),
+                              "volume": round(hostmem.huge_fraction(host_bufs[1]), 3)}
         host_bufs[0].copy_(data)
     tun = tuning.lookup(w.L, args.dtype, "soft")
     if args.tuning:
@@ -707,7 +712,7 @@ def run_ours(args, dist: Dist) -> dict | None:
     # --- end to end through the public API with host buffers
     if not args.no_e2e:
         from paper_1401_7494_gb300 import hostmem
-        pinned, vol_host = host_bufs
+        pinned, vol_host = (hostmem.finish(b) for b in host_bufs)
         host_bufs = None
         for _ in range(max(1, args.warmup)):
             bp.reset(stream)
@@ -790,7 +795,8 @@ def run_ours(args, dist: Dist) -> dict | None:
                                 "the volume read-back overlaps the last pass)",
                          "ms_per_step": round(e_ms / e_steps, 3)}
         e2e_detail = {"host_buffers_huge_page_fraction": {"projections": round(hostmem.huge_fraction(pinned), 3),
-                                                          "volume": round(hostmem.huge_fraction(vol_host), 3)},
+                                                          "volume": round(hostmem.huge_fraction(vol_host), 3),
+                                                          "at_allocation": huge_at_allocation},
                       "step_ms": {"min": round(per_step[0], 3), "median": round(statistics.median(per_step), 3),
                                   "max": round(per_step[-1], 3), "in_order": [round(t, 2) for t in in_order]},
                       "host_enqueue_ms": [round(t, 2) for t in enqueue],

@@ -106,14 +106,16 @@ def _map_chunk(libc, addr: int, n: int) -> None:
     libc.madvise(addr, n, _MADV_COLLAPSE)          # best effort: fails harmlessly where unsupported
 
 
-def pinned_empty(shape, dtype, tries: int = 3):
+def pinned_empty(shape, dtype, tries: int = 3, register: bool = True):
     """A page-locked, huge-page-backed host tensor of ``shape`` and ``dtype`` (contents zero).
 
     The buffer is mapped one huge page at a time inside an aligned reserved range (at most 64 of them; more,
     smaller huge pages are mapped in one go); a huge page that comes back in base pages (a host whose free
     memory is fragmented) is mapped again, up to ``tries`` times, each attempt asking the kernel to compact
-    memory for it.  What still fails stays in base pages: the buffer
-    works, more slowly on such hosts (``huge_fraction`` tells)."""
+    memory for it.  What still fails stays in base pages: the buffer works, more slowly on such hosts
+    (``huge_fraction`` tells).  With ``register=False`` the buffer is neither locked nor registered yet:
+    ``finish`` (on the returned tensor) retries the collapse of the pages still in base pages, which gives
+    the host time to free whole huge pages, then locks and registers it."""
     import torch
     libc = _c()
     n = 1
@@ -154,17 +156,48 @@ def pinned_empty(shape, dtype, tries: int = 3):
                 if _huge_bytes(start, start + size) - before >= hp:
                     break
     mapping = _Mapping.from_address(start)
+    mapping.span = (start, size, hp if huge and size // hp <= 64 else 0)
     t = torch.frombuffer(mapping, dtype=torch.uint8)
     if not huge:
         t.zero_()                                 # touch every page before it is locked
+    out = t[:nbytes].view(dtype).view(*[int(s) for s in shape])
+    out._hostmem_mapping = mapping
+    if register:
+        _lock_and_register(mapping)
+    return out
+
+
+def _lock_and_register(mapping) -> None:
+    import torch
+    start, size, _ = mapping.span
     # Locked pages sit on the unevictable list, out of the reclaim scans (process-local; released with the
     # mapping).  A refusal (a memory-lock limit) leaves the buffer as it is.
-    libc.mlock(start, size)
-    err = cudart.cudaHostRegister(start, size, 0)
+    _c().mlock(start, size)
+    err = torch.cuda.cudart().cudaHostRegister(start, size, 0)
     if int(err) != 0:
         raise RuntimeError(f"cudaHostRegister of {size} bytes failed: {err}")
     mapping.registered = True
-    return t[:nbytes].view(dtype).view(*[int(s) for s in shape])
+
+
+def finish(t, tries: int = 3):
+    """Lock and register a buffer from ``pinned_empty(..., register=False)`` (``t`` is the tensor it
+    returned), first asking again, up to ``tries`` times per huge page, for huge pages where base pages
+    still back it (the contents are kept).  A registered buffer is returned unchanged."""
+    mapping = getattr(t, "_hostmem_mapping", None)
+    if mapping is None:
+        raise ValueError("finish: not a tensor returned by hostmem.pinned_empty")
+    if mapping.registered:
+        return t
+    start, size, hp = mapping.span
+    if hp:
+        libc = _c()
+        for at in range(start, start + size, hp):
+            for _ in range(max(1, tries)):
+                if _huge_bytes(start, start + size) >= size:
+                    break
+                libc.madvise(at, hp, _MADV_COLLAPSE)
+    _lock_and_register(mapping)
+    return t
 
 
 def huge_fraction(t) -> float:

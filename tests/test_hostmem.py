@@ -119,3 +119,19 @@ def test_buffer_is_locked_where_the_limit_allows(fake):
         assert _locked_bytes(t.data_ptr()) >= t.numel() * t.element_size()
     t[:] = 1.0
     assert float(t.sum()) == 1024.0
+
+
+def test_deferred_registration(fake):
+    """register=False leaves the buffer unregistered until finish(), which keeps its contents, registers it
+    once and refuses tensors that do not come from pinned_empty."""
+    t = hostmem.pinned_empty((4096,), torch.float32, register=False)
+    assert t.data_ptr() not in fake.registered
+    t[:] = torch.arange(4096, dtype=torch.float32)
+    assert hostmem.finish(t) is t
+    assert t.data_ptr() in fake.registered and fake.registered[t.data_ptr()] >= 4096 * 4
+    assert torch.equal(t, torch.arange(4096, dtype=torch.float32))
+    n = len(fake.registered)
+    hostmem.finish(t)
+    assert len(fake.registered) == n
+    with pytest.raises(ValueError):
+        hostmem.finish(torch.zeros(4))
