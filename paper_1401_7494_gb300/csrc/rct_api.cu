@@ -1173,15 +1173,10 @@ rct_status backproject_host_impl(rct_ctx *c, const void *h_proj, int first_view,
 
     BpParams p;
     init_params(c, &p);
-    // The first pass waits for its batch to cross the host link, so it takes a quarter of K views: its
-    // upload is a quarter as long and the next batch streams in under it.  Each voxel's sum runs in view
-    // order whatever the pass lengths (partial sums round-trip through the FP32 volume exactly), so the
-    // result is unchanged; the view split regroups each pass's views, so with it every pass keeps K views.
-    const int first = (c->tune.view_split <= 1 && n > K) ? std::max(1, K / 4) : K;
-    int batch = 0, kb = 0;
-    for (int b = 0; b < n; b += kb, ++batch) {
+    int batch = 0;
+    for (int b = 0; b < n; b += K, ++batch) {
         const int g = batch & 1;
-        kb = std::min(batch == 0 ? first : K, n - b);
+        const int kb = std::min(K, n - b);
         // copy stream: wait until group g's previous pass is done, then fill it
         RCT_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_free[g], 0), "cudaStreamWaitEvent");
         p.K = kb;
