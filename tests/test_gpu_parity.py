@@ -141,10 +141,13 @@ def test_split_calls_and_checkpoint_resume(small_cases, cuda_device):
 
 
 def test_host_input_path_matches_device_path(small_cases):
+    """The host-input path (batched uploads and staging on the copy stream) gives the device path's volume bit
+    for bit, for every gather route and a ragged last batch."""
     w, proj, host = small_cases["L40"]
-    for gather in (rct.RCT_GATHER_TLD4, rct.RCT_GATHER_LDG, rct.RCT_GATHER_MIX, rct.RCT_GATHER_QUAD,
-                   rct.RCT_GATHER_PAIR):
-        tun = dict(views_per_pass=5, gather=gather, zrun=4, tex_zrun=1)
+    for gather, K in ((rct.RCT_GATHER_TLD4, 5), (rct.RCT_GATHER_LDG, 5), (rct.RCT_GATHER_MIX, 5),
+                      (rct.RCT_GATHER_QUAD, 5), (rct.RCT_GATHER_PAIR, 5), (rct.RCT_GATHER_PAIR, 24),
+                      (rct.RCT_GATHER_DQUAD, 16)):
+        tun = dict(views_per_pass=K, gather=gather, zrun=4, tex_zrun=1)
         dev = gpu_backproject(w, proj, tuning=tun)
         pinned = torch.from_numpy(host).pin_memory()
         stream = torch.cuda.current_stream()
@@ -155,7 +158,7 @@ def test_host_input_path_matches_device_path(small_cases):
             torch.cuda.synchronize()
             bp.read_volume(out, stream)
             torch.cuda.synchronize()
-        assert np.array_equal(out, dev), f"gather {gather}"
+        assert np.array_equal(out, dev), f"gather {gather}, K={K}"
 
 
 def test_reset_and_zero_volume(small_cases, cuda_device):
