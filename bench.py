@@ -472,17 +472,21 @@ def k_sweep(dev, stream, peaks: dict) -> dict:
 # of the 210 GB/s these hosts sustain from page-locked memory; the wait for it is bounded.
 LINK_READY_GBS = 100.0
 LINK_WAIT_S = 90.0
+LINK_WAIT_TOTAL_S = 150.0      # over the whole run (the end-to-end leg and the three served modes)
+_link_wait_spent = [0.0]
 
 def wait_for_host_link(h2d_gbs, first: float) -> dict:
     """Wait, up to LINK_WAIT_S in 5 s steps, until h2d_gbs() (the rate of a plain host-to-device copy, GB/s;
     ``first`` is the rate already measured) reaches LINK_READY_GBS.  Returns the wait and the rates seen."""
     out = {"seconds": 0.0, "h2d_samples": []}
     rate = first
-    while rate < LINK_READY_GBS and out["seconds"] < LINK_WAIT_S:
+    limit = min(LINK_WAIT_S, LINK_WAIT_TOTAL_S - _link_wait_spent[0])
+    while rate < LINK_READY_GBS and out["seconds"] < limit:
         time.sleep(5.0)
         out["seconds"] += 5.0
         rate = h2d_gbs()
         out["h2d_samples"].append(round(rate, 1))
+    _link_wait_spent[0] += out["seconds"]
     return out
 
 

@@ -139,9 +139,15 @@ def test_wait_for_host_link_is_bounded(monkeypatch):
     """The end-to-end and served legs wait for a plain host-to-device copy at half the link's rate, in 5 s
     steps, and give up after LINK_WAIT_S; a ready link costs no wait."""
     monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+    monkeypatch.setattr(bench, "_link_wait_spent", [0.0])
     assert bench.wait_for_host_link(lambda: 0.0, 210.0) == {"seconds": 0.0, "h2d_samples": []}
     rates = iter([2.7, 9.4, 209.9])
     got = bench.wait_for_host_link(lambda: next(rates), 1.9)
     assert got == {"seconds": 15.0, "h2d_samples": [2.7, 9.4, 209.9]}
+    monkeypatch.setattr(bench, "_link_wait_spent", [0.0])
     slow = bench.wait_for_host_link(lambda: 3.0, 3.0)
     assert slow["seconds"] == bench.LINK_WAIT_S and len(slow["h2d_samples"]) == int(bench.LINK_WAIT_S / 5)
+    # the waits of one run share a total bound
+    rest = bench.wait_for_host_link(lambda: 3.0, 3.0)
+    assert rest["seconds"] == bench.LINK_WAIT_TOTAL_S - bench.LINK_WAIT_S
+    assert bench.wait_for_host_link(lambda: 3.0, 3.0)["seconds"] == 0.0
